@@ -1,0 +1,220 @@
+"""Seeded synthetic inputs for the linear response eigenvalue problem (LREP).
+
+This module only builds inputs: matrices K, M (or the stencil coefficients),
+nullspace bases and random start blocks.  It holds none of the solver's
+arithmetic, so both the CUDA path and the CPU oracle may import it.
+
+Workloads (shapes follow the paper's examples, Section 4):
+
+* ``haar_dense``: K = Q1 diag(k) Q1^T, M = Q2 diag(m) Q2^T with Haar-random
+  orthogonal Q1, Q2 (QR of a Gaussian matrix with the sign of diag(R) folded
+  into Q, Mezzadri's recipe) and spectra k, m drawn uniform or log-uniform.
+  Setting some k to zero gives K a known nullspace spanned by the matching
+  columns of Q1 (Lemma "generalized nullspace": zero eigenvalues of H).
+* ``tridiag_T``: the matrices T(s) of Examples 1 and 2 (1-D finite
+  differences; T(0) Dirichlet, T(-1) periodic and singular).
+* ``bdg_stencil``: a 7-point finite-difference analogue of the 3-D BdG
+  example (Example "large-scale dense matrix"): K = -1/2 Lap_h + d_K,
+  M = -1/2 Lap_h + d_M on a cell-centred grid in (-1/2, 1/2)^3 with a
+  Dirichlet (zero ghost) boundary.  The condensate phi is a Gaussian of
+  widths 1/sqrt(omega0*gamma_d), gamma = (1, 1, 2), normalised to
+  h^3 sum phi^2 = 1, and d_K is chosen pointwise as (1/2 Lap_h phi)/phi so
+  that K phi = 0 exactly: phi is K's null vector, as the condensate is for
+  L_GP in the paper.  d_M = d_K + 2 g phi^2 (the B = g phi^2 coupling).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# dense Haar-built problems
+
+
+def haar_orthogonal(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Haar-distributed orthogonal n x n matrix (QR of N(0,1), signs fixed)."""
+    g = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(g)
+    q *= np.sign(np.diag(r))[None, :]
+    return q
+
+
+def _draw_spectrum(rng, n, lo, hi, law):
+    if law == "uniform":
+        return rng.uniform(lo, hi, size=n)
+    if law == "loguniform":
+        return np.exp(rng.uniform(math.log(lo), math.log(hi), size=n))
+    raise ValueError(law)
+
+
+def haar_dense(n: int, seed: int, k_range=(0.5, 10.0), m_range=(0.5, 10.0),
+               law: str = "uniform", n_zero_k: int = 0, commuting: bool = False):
+    """Dense K, M built from chosen spectra and Haar bases.
+
+    Returns a dict with K, M (n x n float64, symmetric), the spectra k, m,
+    the bases Q1, Q2 and X0 = Q1[:, :n_zero_k] (the nullspace of K; the
+    first ``n_zero_k`` entries of k are set to zero after the draw).
+    With ``commuting=True`` Q2 = Q1, so K and M share eigenvectors.
+    """
+    rng = np.random.default_rng(seed)
+    q1 = haar_orthogonal(n, rng)
+    q2 = q1 if commuting else haar_orthogonal(n, rng)
+    k = _draw_spectrum(rng, n, *k_range, law)
+    m = _draw_spectrum(rng, n, *m_range, law)
+    k[:n_zero_k] = 0.0
+    K = (q1 * k[None, :]) @ q1.T
+    M = (q2 * m[None, :]) @ q2.T
+    K = 0.5 * (K + K.T)
+    M = 0.5 * (M + M.T)
+    return {"K": K, "M": M, "k": k, "m": m, "Q1": q1, "Q2": q2,
+            "X0": q1[:, :n_zero_k].copy(), "r": n_zero_k}
+
+
+def tridiag_T(n: int, s: float) -> np.ndarray:
+    """T(s): 2 on the diagonal, -1 off it, s in the two corners (Section 4)."""
+    t = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    t[0, n - 1] += s
+    t[n - 1, 0] += s
+    return t
+
+
+# --------------------------------------------------------------------------
+# 7-point BdG-like stencil
+
+
+def bdg_stencil(nx: int, ny: int = None, nz: int = None, g: float = 1.0,
+                omega0: float = 100.0, gamma=(1.0, 1.0, 2.0),
+                shift_c: float = None):
+    """Stencil coefficients of the BdG-like workload on an nx*ny*nz grid.
+
+    Grid index i + nx*(j + ny*k) (x fastest), h = 1/nx, points
+    x_i = -1/2 + (i + 1/2) h.  Returns dict with dK, dM (n vectors), phi
+    (the exact null vector of K, unit 2-norm), h and the grid sizes.
+
+    ``shift_c``: if given, d_M = d_K + shift_c instead of d_K + 2 g phi^2
+    (with g = 0 this is the separable special case whose spectrum is known
+    from 1-D eigenvalues).
+    """
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    h = 1.0 / nx
+    dims = (nx, ny, nz)
+    coords = [-0.5 + (np.arange(d) + 0.5) * h for d in dims]
+    omegas = [omega0 * gm for gm in gamma]
+    # 1-D factors: phi = prod_d exp(-omega_d x_d^2 / 2); v_d = 1/2 (r+ + r- - 2)/h^2
+    phis, vs = [], []
+    for x, om, d in zip(coords, omegas, dims):
+        phis.append(np.exp(-0.5 * om * x * x))
+        rp = np.exp(-0.5 * om * (2.0 * x * h + h * h))   # phi(x+h)/phi(x)
+        rm = np.exp(-0.5 * om * (-2.0 * x * h + h * h))  # phi(x-h)/phi(x)
+        rp[-1] = 0.0  # zero ghost beyond the last point
+        rm[0] = 0.0   # zero ghost before the first point
+        vs.append(0.5 * (rp + rm - 2.0) / (h * h))
+    # assemble with x fastest: array shape (nz, ny, nx)
+    px, py, pz = phis
+    vx, vy, vz = vs
+    phi = pz[:, None, None] * py[None, :, None] * px[None, None, :]
+    dK = vz[:, None, None] + vy[None, :, None] + vx[None, None, :]
+    phi = phi.reshape(-1)
+    dK = dK.reshape(-1).copy()
+    # normalise h^3 sum phi^2 = 1 for the coupling term
+    phi_n = phi / math.sqrt(h ** 3 * float(np.dot(phi, phi)))
+    if shift_c is not None:
+        dM = dK + shift_c
+    else:
+        dM = dK + 2.0 * g * phi_n * phi_n
+    unit = phi / np.linalg.norm(phi)
+    return {"dK": dK, "dM": dM, "phi": unit, "h": h, "nx": nx, "ny": ny,
+            "nz": nz, "n": nx * ny * nz, "v1d": vs, "coords": coords,
+            "lap_coef": -0.5}
+
+
+def stencil_to_csr(nx, ny, nz, h, lap_coef, diag):
+    """The stencil operator lap_coef*Lap_h + diag(diag) as CSR arrays.
+
+    Returns (rowptr int64, colind int32, values float64); rows are sorted
+    by column.  Input construction only (used to feed the CSR form).
+    """
+    n = nx * ny * nz
+    c = lap_coef / (h * h)
+    idx = np.arange(n, dtype=np.int64)
+    i = idx % nx
+    j = (idx // nx) % ny
+    k = idx // (nx * ny)
+    cols, vals, rows = [], [], []
+    rows.append(idx); cols.append(idx); vals.append(diag - 6.0 * c)
+    for (cond, off) in ((i > 0, -1), (i < nx - 1, 1), (j > 0, -nx),
+                        (j < ny - 1, nx), (k > 0, -nx * ny),
+                        (k < nz - 1, nx * ny)):
+        r = idx[cond]
+        rows.append(r); cols.append(r + off); vals.append(np.full(r.size, c))
+    rows = np.concatenate(rows); cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return rowptr, cols.astype(np.int32), vals.astype(np.float64)
+
+
+def dense_to_csr(A: np.ndarray, drop: float = 0.0):
+    """CSR arrays of a dense matrix (entries with |a| <= drop omitted)."""
+    n = A.shape[0]
+    mask = np.abs(A) > drop
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum(mask.sum(axis=1))
+    r, c = np.nonzero(mask)
+    return rowptr, c.astype(np.int32), A[r, c].astype(np.float64)
+
+
+# --------------------------------------------------------------------------
+# random start blocks and the serving trace
+
+
+def start_block(n: int, ncols: int, seed: int):
+    """Two independent N(0,1) blocks (U0, V0), n x ncols, column-major."""
+    rng = np.random.default_rng(seed)
+    u = np.asfortranarray(rng.standard_normal((n, ncols)))
+    v = np.asfortranarray(rng.standard_normal((n, ncols)))
+    return u, v
+
+
+def serving_trace(num: int = 1000, seed: int = 4, rate_hz: float = 200.0,
+                  n_lo: int = 256, n_hi: int = 4096, nevs=(4, 8, 16, 32)):
+    """Poisson arrivals with log-uniform n and uniform nev."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_hz, size=num)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    ns = np.floor(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=num))).astype(int)
+    nev = rng.choice(np.asarray(nevs), size=num)
+    return [{"t": float(t), "n": int(nn), "nev": int(e), "seed": 1000 + i}
+            for i, (t, nn, e) in enumerate(zip(arrivals, ns, nev))]
+
+
+# --------------------------------------------------------------------------
+# the configurations the solver is measured on
+
+
+def config(idx: int):
+    """Problem description of workload ``idx`` (0..3); see module docstring."""
+    if idx == 0:
+        p = haar_dense(200, seed=0)
+        p.update(nev=4, block=4, tol=1e-10, name="dense-fp64-n200")
+        return p
+    if idx == 1:
+        p = haar_dense(8192, seed=1, n_zero_k=4)
+        p.update(nev=64, block=16, tol=1e-10, name="dense-fp64-n8192-null4")
+        return p
+    if idx == 2:
+        p = bdg_stencil(64)
+        p.update(nev=32, block=16, tol=1e-10, name="stencil-bdg-64^3", r=1,
+                 X0=p["phi"][:, None].copy())
+        return p
+    if idx == 3:
+        p = haar_dense(32768, seed=3, k_range=(1e-2, 1e2), m_range=(1e-2, 1e2),
+                       law="loguniform")
+        p.update(nev=256, block=32, tol=1e-8, name="dense-mixed-n32768")
+        return p
+    raise ValueError(idx)
