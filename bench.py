@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 BOSP solver: eigenpairs/s at residual <= tol.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp64|mixed]
+
+One step is one complete solve (Alg. 2 with the moving window) of the dense
+n = 8192 workload: K, M built from chosen spectra with Haar bases, k and m
+uniform in [0.5, 10], four zero k (nullspace of K, deflated through V0),
+nev = 64 in moving-window batches of nb = 16, tol 1e-10.  The operator
+(2 x 537 MB) is resident in HBM before the clock starts and is larger than
+L2, so no flush is needed between steps.  value = eigenpairs per second
+over the K timed steps (all ranks; every rank solves its own replica, the
+solver does not shard: "replicas only").
+
+Also reported: the dominant kernel's roofline (the float64 dense product,
+timed per launch with CUDA events on the solver's stream), an end-to-end
+figure through the C ABI from pinned host buffers, the CPU oracle as a
+baseline, and the SM clocks sampled during the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 nominal (unit counts x clock)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(precision):
+    from paper_2506_08355_gb300 import synth
+    p = synth.config(1)
+    return p, {"workload": "dense-lrep-n8192-nev64-block16-null4-tol1e-10",
+               "n": 8192, "nev": 64, "block": 16, "tol": 1e-10, "nullspace": 4,
+               "spectra": "k, m ~ U[0.5, 10], Haar Q1, Q2 (seed 1)",
+               "precision": precision, "window": "moving, s = 3",
+               "l2": "operator 1.07 GB resident, larger than L2 (no flush)"}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+
+def oracle_sample(p, sample_iters, full_iters):
+    """Time the FP64 oracle (literal Alg. 2) for a bounded number of outer
+    iterations on the same workload and scale to a full solve by the
+    iteration count of a full solve."""
+    from oracle import lrep_ref as R
+    op = R.DenseOp(p["K"], p["M"])
+    t0 = time.perf_counter()
+    R.bosp(op, p["nev"], p["block"], p["tol"], X0=p["X0"], max_iters=sample_iters)
+    dt = time.perf_counter() - t0
+    per_it = dt / sample_iters
+    est = per_it * full_iters
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": p["nev"] / est, "unit": "eigenpairs/s", "cores": cores,
+            "kind": "oracle",
+            "sample": "numpy FP64 oracle (literal Alg. 2), first %d outer iterations of "
+                      "the same n=8192 workload in %.1f s (%.2f s/iteration, numpy BLAS "
+                      "threads = cores), scaled to a full solve of %d iterations"
+                      % (sample_iters, dt, per_it, full_iters),
+            "seconds": dt}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    p, cfg = workload("fp64")
+    full_iters = 0
+    gold = os.path.join(ROOT, "tests", "golden", "config1_oracle_run.txt")
+    if os.path.exists(gold):
+        for line in open(gold):
+            if line.startswith("iters"):
+                full_iters = int(line.split()[1])
+    full_iters = full_iters or 100
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(p, 2, full_iters)
+        if s >= args.warmup:
+            vals.append(r)
+    v = float(np.mean([r["value"] for r in vals]))
+    base = dict(vals[-1])
+    base["value"] = v
+    line = {"impl": "reference", "metric": "eigenpairs/s at residual<=1e-10 (FP64 path)",
+            "value": v, "unit": "eigenpairs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * p["nev"] / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": cfg, "cpu_baseline": base,
+            "e2e": {"value": v, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- ours
+
+
+def main():
+    args = parse()
+    rank, world, local = dist()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=dev)
+        pg = td
+    from paper_2506_08355_gb300 import build, lrep
+    build.build()
+    p, cfg = workload(args.precision)
+    nev, nb, tol = p["nev"], p["block"], p["tol"]
+    prec = lrep.PREC_FP64 if args.precision == "fp64" else lrep.PREC_MIXED_BF16X3
+    stream = torch.cuda.Stream(device=dev)
+    Kd = torch.from_numpy(p["K"]).to(dev)
+    Md = torch.from_numpy(p["M"]).to(dev)
+    prob = lrep.Problem.dense(Kd, Md, borrow=True, stream=stream)
+    prob.set_nullspace(p["X0"])
+    prob.set_options(precision=prec, profile=0)
+    for _ in range(args.warmup):
+        st = prob.solve(nev, nb, tol)
+        assert st == lrep.OK, st
+    # timed region: K complete solves, events on the solver's stream
+    clocks = Clocks(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = lrep.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        st = prob.solve(nev, nb, tol)
+        assert st == lrep.OK, st
+        iters.append(prob.iters())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = lrep.launch_count() - l0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        pg.barrier()
+    ms_step = ms / args.steps
+    value = world * nev * args.steps / (ms / 1000.0)
+    res = prob.residuals()
+    assert prob.nconv() == nev and res.max() < tol, (prob.nconv(), res.max())
+    # roofline of the dominant kernel: one more profiled solve (per-launch
+    # CUDA events on the solver's stream)
+    prob.set_options(precision=prec, profile=1)
+    prob.solve(nev, nb, tol)
+    prof = prob.profile()
+    prob.set_options(precision=prec, profile=0)
+    launches_p = max(prof[1], 1.0)
+    avg_s = prof[0] / launches_p
+    flops_launch = prof[2] / launches_p
+    bytes_launch = prof[3] / launches_p
+    peaks = measured_peaks()
+    roof = {"kernel": "dense_apply_f64 (+ split-K reduce)", "bound": "alu",
+            "achieved": flops_launch / avg_s / 1e12, "peak": FP64_PEAK_GFLOPS / 1e3,
+            "unit": "TFLOP/s", "frac": (flops_launch / avg_s / 1e9) / FP64_PEAK_GFLOPS,
+            "traffic": None, "algorithmic_flops_per_launch": flops_launch,
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "avg_launch_ms": avg_s * 1e3, "launches_per_solve": prof[1],
+            "hbm_gbs_achieved": bytes_launch / avg_s / 1e9,
+            "hbm_frac_of_measured": (bytes_launch / avg_s / 1e9) / peaks.get("hbm_gbs", 6780.7),
+            "peak_note": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak); HBM of measured"}
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Kh = torch.from_numpy(p["K"]).pin_memory()
+        Mh = torch.from_numpy(p["M"]).pin_memory()
+        times = []
+        d2h = 0
+        for s in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q = lrep.Problem.dense(Kh.numpy(), Mh.numpy(), stream=stream)
+            q.set_nullspace(p["X0"])
+            q.set_options(precision=prec)
+            st = q.solve(nev, nb, tol)
+            lam = q.eigvals()
+            X = q.vectors(lrep.Q_X)
+            Y = q.vectors(lrep.Q_Y)
+            times.append(time.perf_counter() - t0)
+            d2h = lam.nbytes + X.nbytes + Y.nbytes
+            q.close()
+        h2d = 2 * p["K"].nbytes + p["X0"].nbytes
+        e2e = {"value": world * nev / float(np.mean(times)), "unit": "eigenpairs/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "seconds_per_step": float(np.mean(times))}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            cpu = oracle_sample(p, 3, int(np.mean(iters)))
+        except Exception as ex:  # reported, not fatal
+            cpu = {"error": str(ex)}
+    if rank == 0:
+        line = {"metric": "eigenpairs/s at residual<=1e-10 (%s path)" % args.precision.upper(),
+                "value": value, "unit": "eigenpairs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "bf16x3+f64",
+                "data": "synthetic", "config": cfg,
+                "outer_iterations": iters, "max_residual": float(res.max()),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk,
+                "parallelism": "replicas only (%d)" % world}
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,96 @@
+/*
+ * lrep_ops.h - the hot-path steps of one BOSP iteration as separate
+ * C entry points, for callers that drive their own iteration and for
+ * step-by-step verification.  All pointers are DEVICE pointers unless a
+ * parameter name ends in _host; blocks are column-major float64; every
+ * call is asynchronous on `stream` (a cudaStream_t, NULL = legacy default)
+ * except those returning a count through a _host pointer, which
+ * synchronise that stream.  Return values are lrep_status codes.
+ * Scratch memory is drawn from a per-device pool owned by the library
+ * (grown with cudaMalloc on first use, kept until process exit); calls
+ * that share a device and overlap in time must use one stream.
+ */
+#ifndef LREP_OPS_H
+#define LREP_OPS_H
+
+#include <stdint.h>
+
+#include "lrep.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Step 3 / Step 6 products: Y = K X (op = LREP_OP_K) or Y = M X
+ * (LREP_OP_M) for ncols columns of a problem's operator (dense, CSR,
+ * stencil or callback), in the problem's precision for float64 products
+ * (Section 3.2, "(2d) mv" of the Step 3 cost).  Runs on the problem's
+ * stream. */
+lrep_status lrep_op_apply(lrep_problem p, int32_t op, int32_t ncols,
+                          const double* X, int64_t ldx, double* Y, int64_t ldy);
+
+/* Same as lrep_op_apply but with the problem's low-precision CG operator
+ * (MIXED_BF16X3: hi/lo bfloat16 split of K or M, fp32 accumulation);
+ * identical to lrep_op_apply for FP64 problems. */
+lrep_status lrep_op_apply_cg(lrep_problem p, int32_t op, int32_t ncols,
+                             const double* X, int64_t ldx, double* Y,
+                             int64_t ldy);
+
+/* Tall-skinny Gram G = A^T B (A n x a, B n x b), the inner products of
+ * eq. hat_H (K^ = U^T K U, M^ = V^T M V) and eq. update_W/Z.  G is a x b
+ * with leading dimension ldg.  Deterministic (fixed reduction order). */
+lrep_status lrep_op_gram(int64_t n, int32_t a, int32_t b, const double* A,
+                         int64_t lda, const double* B, int64_t ldb, double* G,
+                         int64_t ldg, void* stream);
+
+/* Block update C = alpha C + beta A B (A n x k, B k x c): the Ritz
+ * pullback X~ = U X^ (eq. eigenVector-pullback) and the projection of
+ * eq. update_W/Z.  C must not overlap A. */
+lrep_status lrep_op_update(int64_t n, int32_t k, int32_t c, double alpha,
+                           const double* A, int64_t lda, const double* B,
+                           int64_t ldb, double beta, double* C, int64_t ldc,
+                           void* stream);
+
+/* Small projected LREP (eq. small_eigen) of order d <= 256: K^, M^ are
+ * d x d (leading dimension ld; symmetrised as (G + G^T)/2).  Writes the d
+ * eigenvalues ascending to lam[d] and X^, Y^ (d x d, leading dimension
+ * ldo) with K^ X^ = Y^ diag(lam), M^ Y^ = X^ diag(lam), X^T Y^ = I, by two
+ * Cholesky factorisations and a one-sided Jacobi SVD.  *info_host: 0 ok,
+ * 1 K^ not SPD, 2 M^ not SPD, 3 SVD did not converge. */
+lrep_status lrep_op_small_lrep(int32_t d, const double* Khat,
+                               const double* Mhat, int32_t ld, double* lam,
+                               double* Xh, double* Yh, int32_t ldo,
+                               int32_t* info_host, void* stream);
+
+/* Alg. 1 (MGS-Biorth) of the pair (W, Z), n x m, with the discard rule of
+ * the Remark after it (|eta| <= tau ||w_l|| ||z_l||).  Writes the kept
+ * pairs to P, Q (n x kept, leading dimension ldo; must not overlap W, Z)
+ * and the count to *kept_host.  P^T Q = I. */
+lrep_status lrep_op_biorth(int64_t n, int32_t m, const double* W,
+                           const double* Z, int64_t ld, double tau, double* P,
+                           double* Q, int64_t ldo, int32_t* kept_host,
+                           void* stream);
+
+/* eq. tol residuals: eps_i = ||[KX_i - lam_i Y_i; MY_i - lam_i X_i]|| /
+ * ((1 + lam_i) ||[Y_i; X_i]||) for w columns (all blocks share ld). */
+lrep_status lrep_op_residuals(int64_t n, int32_t w, const double* X,
+                              const double* Y, const double* KX,
+                              const double* MY, int64_t ld, const double* lam,
+                              double* eps, void* stream);
+
+/* Step 1 random start: n x ncols N(0,1) block from Philox4x32-10 with key
+ * (seed_lo, seed_hi) and counter (t lo, t hi, stream_id, 0), t = e / 2 for
+ * element e = row + n * col, two normals per counter by Box-Muller on the
+ * first two output words (u = (w + 0.5) / 2^32). */
+lrep_status lrep_op_philox_normal(int64_t n, int32_t ncols, uint64_t seed,
+                                  int32_t stream_id, double* out, int64_t ld,
+                                  void* stream);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all problems); a monotone counter for accounting. */
+int64_t lrep_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LREP_OPS_H */

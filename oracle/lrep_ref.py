@@ -161,6 +161,14 @@ def lrep_definition(K, M, nev, r=0, FK=None, FM=None):
     return sig, X, Y
 
 
+def lrep_definition_values(FK, FM, nev, r=0):
+    """Eigenvalues only of the definition route (one values-only SVD of
+    F_K^T F_M), for orders where the vectors are not needed.
+    Parity: pinned against ``lrep_definition`` (same singular values)."""
+    sig = np.sort(np.linalg.svd(FK.T @ FM, compute_uv=False))
+    return sig[r:r + nev]
+
+
 def fix_sign(X, Y):
     """Scale pair columns by +-1 so that the largest-|.| entry of x is > 0."""
     X = np.array(X, dtype=np.float64, copy=True)

@@ -1,0 +1,785 @@
+// Host driver of the BOSP iteration (Alg. 2 with the moving window of
+// Section 3.3).  Every arithmetic step runs in the library's kernels on the
+// problem's stream; the host keeps only the control state (window position,
+// locked count, active set) and reads back a few scalars per iteration.
+//
+// Block layout: all n-row blocks are column-major with ld = n rounded up to
+// 32.  U = [X | P | W] and V = [Y | Q | Z] live in two double-buffered
+// arrays together with K U and M V; the next basis is assembled in the
+// other buffer: Ritz vectors of the projected problem (pullback) at their
+// Ritz index, followed by P~ and W~ after the window.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "problem.h"
+
+namespace lrep {
+
+cudaError_t Arena::reserve(size_t bytes) {
+  release();
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMalloc(&base, bytes);
+  if (e != cudaSuccess) {
+    base = nullptr;
+    return e;
+  }
+  cap = bytes;
+  off = 0;
+  return cudaMemset(base, 0, bytes);
+}
+
+void Arena::release() {
+  if (base) cudaFree(base);
+  base = nullptr;
+  cap = off = 0;
+}
+
+size_t apply_ws_elems(lrep_problem p, int c) {
+  if (p->op.kind == OP_DENSE) return dense_apply_ws_elems(p->op.n, c);
+  return 0;
+}
+
+lrep_status apply_op(lrep_problem p, int which, int c, const double* X,
+                     int64_t ldx, double* Y, int64_t ldy, const int* skip,
+                     double* ws, size_t ws_elems) {
+  Operator& o = p->op;
+  cudaError_t e = cudaSuccess;
+  const bool isK = (which == LREP_OP_K);
+  switch (o.kind) {
+    case OP_DENSE:
+      e = dense_apply_f64(o.n, c, isK ? o.K : o.M, o.ld, X, ldx, Y, ldy, ws,
+                          ws_elems, skip, p->stream);
+      break;
+    case OP_CSR:
+      e = csr_apply_f64(o.n, isK ? o.rpK : o.rpM, isK ? o.ciK : o.ciM,
+                        isK ? o.vK : o.vM, c, X, ldx, Y, ldy, skip, p->stream);
+      break;
+    case OP_STENCIL:
+      e = stencil_apply_f64(o.nx, o.ny, o.nz, o.coef_h2, isK ? o.dK : o.dM, c,
+                            X, ldx, Y, ldy, skip, p->stream);
+      break;
+    case OP_CALLBACK: {
+      if (skip) {
+        int h = 0;
+        e = cudaMemcpyAsync(&h, skip, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) break;
+        if (h) return LREP_OK;
+      }
+      const int rc = o.fn(o.user, which, o.n, c, X, ldx, Y, ldy, (void*)p->stream);
+      if (rc != 0)
+        return p->fail(LREP_ERR_CALLBACK, "operator callback returned " + std::to_string(rc));
+      e = cudaGetLastError();
+      break;
+    }
+    default:
+      return p->fail(LREP_ERR_STATE, "unknown operator kind");
+  }
+  if (e != cudaSuccess)
+    return p->fail(LREP_ERR_CUDA, std::string("operator product: ") + cudaGetErrorString(e));
+  return LREP_OK;
+}
+
+namespace {
+
+#define LCK(expr)                                                                   \
+  do {                                                                              \
+    cudaError_t _e = (expr);                                                        \
+    if (_e != cudaSuccess)                                                          \
+      return p->fail(LREP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+#define LST(expr)                      \
+  do {                                 \
+    lrep_status _s = (expr);           \
+    if (_s != LREP_OK) return _s;      \
+  } while (0)
+
+struct Solver {
+  lrep_problem p;
+  cudaStream_t st;
+  int64_t n, ld;
+  int nev, nb, w, r, dmax, C, Lmax, cgcols;
+  bool moving;
+  double tol;
+  // double-buffered bases
+  double* UX[2];
+  double* UY[2];
+  double* KX[2];
+  double* MY[2];
+  int cur = 0;
+  int64_t off = 0;
+  int d = 0;
+  // deflation basis [X0 | locked], [Y0 | locked]; orthonormal basis of X0
+  double *Dx, *Dy, *Q0;
+  // CG and W/Z blocks
+  double *Rhs, *Zr, *Wr, *Rr, *Pr, *Qr, *TW, *TZ;
+  // small matrices
+  double *Kh, *Mh, *Sh, *Xh, *Yh, *swork, *Ph, *Qh, *pqwork, *G2, *cA, *cB, *cA2,
+      *cB2, *cwork, *Cproj;
+  double *lam_d, *eps_d, *berr_d, *refw2, *refz2, *lam_act, *lam_lock;
+  int *info_d, *cnt_d, *act_d;
+  // scratch for reductions and split-K
+  double* ws;
+  size_t ws_elems = 0, part_elems = 0;
+  double* part;
+  double *Rg, *Rinv, *Rwork;  // r x r scratch of the V0 normalisation
+  unsigned int* counters;  // [0] residual [1] colnorm [2..4] cg
+  CgState cg;
+  // pinned host mirror
+  struct Host {
+    double lam[512];
+    double eps[512];
+    double berr;
+    int info;
+    int cnt[4];
+    int cg_iters;
+    int act[64];
+    double lam_act[64];
+  }* h = nullptr;
+  // host control state
+  int ell = 0, w_prev = 0;
+  bool stale = false;
+  std::vector<double> locked;
+  cudaEvent_t ev[6];
+  bool events = false;
+  struct Pending {
+    cudaEvent_t a, b;
+    int c;
+    bool cgop;
+  };
+  std::vector<cudaEvent_t> prof_free, prof_all;
+  std::vector<Pending> prof_pending;
+
+  lrep_status take_event(cudaEvent_t* e) {
+    if (prof_free.empty()) {
+      cudaEvent_t x;
+      LCK(cudaEventCreate(&x));
+      prof_all.push_back(x);
+      prof_free.push_back(x);
+    }
+    *e = prof_free.back();
+    prof_free.pop_back();
+    return LREP_OK;
+  }
+
+  // after a stream synchronisation: account the timed products
+  void resolve_profile() {
+    for (const Pending& q : prof_pending) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, q.a, q.b);
+      account_product(q.c, ms, q.cgop);
+      prof_free.push_back(q.a);
+      prof_free.push_back(q.b);
+    }
+    prof_pending.clear();
+  }
+
+  double* Ucur() { return UX[cur] + off * ld; }
+  double* Vcur() { return UY[cur] + off * ld; }
+  double* KUcur() { return KX[cur] + off * ld; }
+  double* MVcur() { return MY[cur] + off * ld; }
+  int nx() const { return 1 - cur; }
+
+  lrep_status sync() {
+    LCK(cudaStreamSynchronize(st));
+    if (!prof_pending.empty()) resolve_profile();
+    return LREP_OK;
+  }
+
+  // Lays out every device buffer in the arena (dry run when A.base is
+  // null: only the size is computed).
+  void layout(Arena& A) {
+    const int dd = 2 * dmax;
+    const size_t sm = (size_t)dmax * dmax;
+    const int rr = std::max(r, 1);
+    auto blk = [&](int cols) { return A.take<double>((size_t)ld * cols); };
+    for (int b = 0; b < 2; ++b) {
+      UX[b] = blk(C); UY[b] = blk(C); KX[b] = blk(C); MY[b] = blk(C);
+    }
+    Dx = blk(r + nev); Dy = blk(r + nev); Q0 = blk(rr);
+    Rhs = blk(cgcols); Zr = blk(cgcols); Wr = blk(cgcols); Rr = blk(cgcols);
+    Pr = blk(cgcols); Qr = blk(cgcols); TW = blk(cgcols); TZ = blk(cgcols);
+    Kh = A.take<double>(sm); Mh = A.take<double>(sm); Sh = A.take<double>(sm);
+    Xh = A.take<double>(sm); Yh = A.take<double>(sm);
+    swork = A.take<double>(small_work_elems(dmax));
+    Ph = A.take<double>((size_t)dmax * cgcols); Qh = A.take<double>((size_t)dmax * cgcols);
+    pqwork = A.take<double>(pq_work_elems(dmax, cgcols));
+    G2 = A.take<double>((size_t)dd * dd);
+    cA = A.take<double>(sm); cB = A.take<double>(sm);
+    cA2 = A.take<double>(sm); cB2 = A.take<double>(sm);
+    cwork = A.take<double>(biorth_coef_work_elems(dmax));
+    Cproj = A.take<double>((size_t)Lmax * cgcols + (size_t)rr * dmax);
+    Rg = A.take<double>((size_t)rr * rr);
+    Rinv = A.take<double>((size_t)rr * rr);
+    Rwork = A.take<double>((size_t)rr * rr);
+    lam_d = A.take<double>(512); eps_d = A.take<double>(512);
+    berr_d = A.take<double>(64); refw2 = A.take<double>(64); refz2 = A.take<double>(64);
+    lam_act = A.take<double>(64); lam_lock = A.take<double>(std::max(nev, 64));
+    info_d = A.take<int>(64); cnt_d = A.take<int>(64); act_d = A.take<int>(64);
+    ws = A.take<double>(std::max<size_t>(ws_elems, 1));
+    part = A.take<double>(std::max<size_t>(part_elems, 1));
+    counters = A.take<unsigned int>(64);
+    cg.rho = A.take<double>(cgcols); cg.stop = A.take<double>(cgcols);
+    cg.alpha = A.take<double>(cgcols); cg.beta = A.take<double>(cgcols);
+    cg.active = A.take<int>(cgcols); cg.done = A.take<int>(8);
+    cg.iters = A.take<int>(8);
+    cg.part = part;
+    cg.counter = counters + 2;
+  }
+
+  lrep_status alloc() {
+    const size_t key[4] = {(size_t)n, (size_t)nev, (size_t)nb,
+                           (size_t)(w * 1000 + r * 7 + p->opts.precision)};
+    ld = ((n + 31) / 32) * 32;
+    cgcols = std::max(nb, std::max(r, 1));
+    const int dd = 2 * dmax;
+    const int rr = std::max(r, 1);
+    size_t wsz = 0;
+    wsz = std::max(wsz, gram_ws_elems(n, dmax, dmax));
+    wsz = std::max(wsz, gram_ws_elems(n, dd, dd));
+    wsz = std::max(wsz, gram_ws_elems(n, Lmax, cgcols));
+    wsz = std::max(wsz, gram_ws_elems(n, rr, std::max(rr, dmax)));
+    wsz = std::max(wsz, gram_ws_elems(n, nev, nev));
+    wsz = std::max(wsz, apply_ws_elems(p, std::max(C, cgcols)));
+    ws_elems = wsz;
+    part_elems = std::max(residual_ws_elems(n, std::max(C, nev)),
+                          std::max(colnorm_ws_elems(n, cgcols), cg_part_elems(n, cgcols)));
+    Arena dry;
+    dry.base = nullptr;
+    dry.cap = ~(size_t)0;
+    layout(dry);
+    const size_t bytes = dry.off + 4096;
+    Arena& A = p->ws;
+    bool reuse = (A.base != nullptr) && A.cap >= bytes;
+    for (int i = 0; i < 4; ++i) reuse = reuse && p->ws_key[i] == key[i];
+    if (!reuse) {
+      LCK(A.reserve(bytes));
+      for (int i = 0; i < 4; ++i) p->ws_key[i] = key[i];
+    } else {
+      LCK(cudaMemsetAsync(A.base, 0, A.cap, st));
+    }
+    A.off = 0;
+    layout(A);
+    if (A.off > A.cap) return p->fail(LREP_ERR_NOMEM, "workspace layout overflow");
+    LCK(cudaMallocHost(&h, sizeof(Host)));
+    return LREP_OK;
+  }
+
+  void release_host() {
+    if (h) cudaFreeHost(h);
+    h = nullptr;
+    if (!prof_pending.empty() && cudaStreamSynchronize(st) == cudaSuccess) resolve_profile();
+    for (auto& e : prof_all) cudaEventDestroy(e);
+    prof_all.clear();
+    prof_free.clear();
+    if (events)
+      for (auto& e : ev) cudaEventDestroy(e);
+    events = false;
+  }
+
+  // ---------------------------------------------------------- primitives
+  lrep_status gram(const Segs& A, const Segs& B, double* G, int64_t ldg) {
+    LCK(gram_f64(n, A, B, G, ldg, ws, ws_elems, st));
+    return LREP_OK;
+  }
+  lrep_status update(int c, double alpha, const Segs& A, const double* B,
+                     int64_t ldb, double beta, double* Cm) {
+    LCK(update_f64(n, c, alpha, A, B, ldb, beta, Cm, ld, st));
+    return LREP_OK;
+  }
+  lrep_status apply(int which, int c, const double* X, double* Y,
+                    const int* skip = nullptr, bool cgop = false) {
+    if (c <= 0) return LREP_OK;
+    p->matvecs += skip ? 0 : c;
+    const bool prof = p->opts.profile && !skip;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (prof) {
+      LST(take_event(&e0));
+      LST(take_event(&e1));
+      LCK(cudaEventRecord(e0, st));
+    }
+    lrep_status s = cgop ? apply_op_cg(p, which, c, X, ld, Y, ld, skip, ws, ws_elems)
+                         : apply_op(p, which, c, X, ld, Y, ld, skip, ws, ws_elems);
+    if (prof && s == LREP_OK) {
+      LCK(cudaEventRecord(e1, st));
+      prof_pending.push_back(Pending{e0, e1, c, cgop});
+      if (prof_pending.size() > 512) LST(sync());
+    }
+    return s;
+  }
+
+  // algorithmic work of one product of c columns
+  void account_product(int c, float ms, bool cgop) {
+    const Operator& o = p->op;
+    double nnz = 0.0, opbytes = 0.0;
+    if (o.kind == OP_DENSE) {
+      nnz = (double)n * n;
+      opbytes = (cgop && p->opts.precision == LREP_PREC_MIXED_BF16X3) ? 4.0 * nnz : 8.0 * nnz;
+    } else if (o.kind == OP_STENCIL) {
+      nnz = 7.0 * n;
+      opbytes = 8.0 * n;  // the diagonal
+    } else if (o.kind == OP_CSR) {
+      nnz = 7.0 * n;
+      opbytes = 12.0 * nnz + 8.0 * (n + 1);
+    }
+    p->prof[0] += ms * 1e-3;
+    p->prof[1] += 1.0;
+    p->prof[2] += 2.0 * nnz * c;
+    p->prof[3] += opbytes + 16.0 * n * c;
+  }
+
+  // Block CG (one CG per column) for op * X = B; check_every > 0 reads the
+  // done flag every that many iterations (long solves).
+  lrep_status cg_solve(int which, int c, const double* B, double* X, double ctol,
+                       int maxit, int check_every, bool cgop) {
+    LCK(cudaMemsetAsync(cg.iters, 0, sizeof(int), st));
+    LCK(cg_init(n, c, B, ld, X, Rr, Pr, ld, ctol, cg, st));
+    for (int it = 0; it < maxit; ++it) {
+      LST(apply(which, c, Pr, Qr, cg.done, cgop));
+      LCK(cg_alpha(n, c, Pr, Qr, ld, cg, st));
+      LCK(cg_update(n, c, X, Rr, Pr, Qr, ld, cg, st));
+      LCK(cg_pdir(n, c, Rr, Pr, ld, cg, st));
+      if (check_every > 0 && (it + 1) % check_every == 0) {
+        int done = 0;
+        LCK(cudaMemcpyAsync(&h->cnt[3], cg.done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LST(sync());
+        done = h->cnt[3];
+        if (done) break;
+      }
+    }
+    LCK(cudaMemcpyAsync(&h->cg_iters, cg.iters, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LST(sync());
+    p->matvecs += (int64_t)h->cg_iters * c;
+    return LREP_OK;
+  }
+
+  // Alg. 1 for the n x m pair (A, B) in coefficient form, two passes; the
+  // result (kept columns) is written to (outA, outB) and the same
+  // combinations are applied to (KA, MB) when given.  ref2 (device,
+  // squared entering norms) may be null.  Returns the kept count in *kept.
+  lrep_status biorth_block(const double* Ain, const double* Bin, int m,
+                           const double* KA, const double* MB, double* tA,
+                           double* tB, double* tKA, double* tMB, double* outA,
+                           double* outB, double* outKA, double* outMB,
+                           const double* refa2, const double* refb2, int* kept) {
+    const double tau = p->opts.discard_tol;
+    *kept = 0;
+    if (m <= 0) return LREP_OK;
+    const int ldg = 2 * dmax;
+    Segs s = seg_push(seg1(Ain, ld, m), Bin, ld, m);
+    LST(gram(s, s, G2, ldg));
+    LCK(biorth_coef(m, G2, ldg, refa2, refb2, tau, cA, cB, dmax, cwork, cnt_d, st));
+    LCK(cudaMemcpyAsync(&h->cnt[0], cnt_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LST(sync());
+    const int k1 = h->cnt[0];
+    if (k1 == 0) return LREP_OK;
+    LST(update(k1, 0.0, seg1(Ain, ld, m), cA, dmax, 1.0, tA));
+    LST(update(k1, 0.0, seg1(Bin, ld, m), cB, dmax, 1.0, tB));
+    if (KA) {
+      LST(update(k1, 0.0, seg1(KA, ld, m), cA, dmax, 1.0, tKA));
+      LST(update(k1, 0.0, seg1(MB, ld, m), cB, dmax, 1.0, tMB));
+    }
+    Segs s2 = seg_push(seg1(tA, ld, k1), tB, ld, k1);
+    LST(gram(s2, s2, G2, ldg));
+    LCK(biorth_coef(k1, G2, ldg, nullptr, nullptr, tau, cA2, cB2, dmax, cwork, cnt_d, st));
+    LCK(cudaMemcpyAsync(&h->cnt[0], cnt_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LST(sync());
+    const int k2 = h->cnt[0];
+    LST(update(k2, 0.0, seg1(tA, ld, k1), cA2, dmax, 1.0, outA));
+    LST(update(k2, 0.0, seg1(tB, ld, k1), cB2, dmax, 1.0, outB));
+    if (KA) {
+      LST(update(k2, 0.0, seg1(tKA, ld, k1), cA2, dmax, 1.0, outKA));
+      LST(update(k2, 0.0, seg1(tMB, ld, k1), cB2, dmax, 1.0, outMB));
+    }
+    *kept = k2;
+    return LREP_OK;
+  }
+
+  // ------------------------------------------------------------- setup
+  lrep_status setup() {
+    // generalized nullspace (eq. V0_basis)
+    if (r > 0) {
+      LCK(copy_cols(n, r, p->X0in, ld, Dx, ld, st));
+      if (p->Y0in) {
+        LCK(copy_cols(n, r, p->Y0in, ld, Dy, ld, st));
+      } else {
+        LST(cg_solve(LREP_OP_M, r, Dx, Dy, 1e-14, 20000, 50, false));
+      }
+      double* T = UX[1];
+      LST(gram(seg1(Dx, ld, r), seg1(Dy, ld, r), Rg, r));
+      LCK(chol_upper_inverse(r, Rg, r, Rinv, r, Rwork, info_d, st));
+      LST(update(r, 0.0, seg1(Dx, ld, r), Rinv, r, 1.0, T));
+      LCK(copy_cols(n, r, T, ld, Dx, ld, st));
+      LST(update(r, 0.0, seg1(Dy, ld, r), Rinv, r, 1.0, T));
+      LCK(copy_cols(n, r, T, ld, Dy, ld, st));
+      // orthonormal basis of span(X0) for the right-hand sides of K W = ...
+      LCK(copy_cols(n, r, Dx, ld, Q0, ld, st));
+      for (int pass = 0; pass < 2; ++pass) {
+        LST(gram(seg1(Q0, ld, r), seg1(Q0, ld, r), Rg, r));
+        LCK(chol_upper_inverse(r, Rg, r, Rinv, r, Rwork, info_d + 1, st));
+        LST(update(r, 0.0, seg1(Q0, ld, r), Rinv, r, 1.0, T));
+        LCK(copy_cols(n, r, T, ld, Q0, ld, st));
+      }
+      LCK(cudaMemcpyAsync(h->cnt, info_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      LST(sync());
+      if (h->cnt[0] || h->cnt[1])
+        return p->fail(LREP_ERR_ARG, "nullspace basis X0 is rank deficient or X0^T M^-1 X0 not SPD");
+    }
+    // Step 1: random U, V
+    const int d0 = (int)std::min<int64_t>(w + 2 * nb, n - r);
+    if (p->U0 && p->start_cols >= d0) {
+      LCK(copy_cols(n, d0, p->U0, ld, UX[0], ld, st));
+      LCK(copy_cols(n, d0, p->V0, ld, UY[0], ld, st));
+    } else {
+      LCK(philox_normal(n, d0, p->opts.seed, 0, UX[0], ld, st));
+      LCK(philox_normal(n, d0, p->opts.seed, 1, UY[0], ld, st));
+    }
+    // Step 2: project off V0 (twice) and biorthogonalise
+    if (r > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        LST(gram(seg1(Dy, ld, r), seg1(UX[0], ld, d0), Cproj, r));
+        LST(update(d0, 1.0, seg1(Dx, ld, r), Cproj, r, -1.0, UX[0]));
+        LST(gram(seg1(Dx, ld, r), seg1(UY[0], ld, d0), Cproj, r));
+        LST(update(d0, 1.0, seg1(Dy, ld, r), Cproj, r, -1.0, UY[0]));
+      }
+    }
+    int kept = 0;
+    LST(biorth_block(UX[0], UY[0], d0, nullptr, nullptr, UX[1], UY[1], nullptr,
+                     nullptr, UX[0], UY[0], nullptr, nullptr, nullptr, nullptr, &kept));
+    if (kept == 0) return p->fail(LREP_ERR_BREAKDOWN, "start block lost every column");
+    cur = 0; off = 0; d = kept;
+    LST(refresh());
+    w_prev = std::min(w, d);
+    return LREP_OK;
+  }
+
+  lrep_status refresh() {
+    LST(apply(LREP_OP_K, d, Ucur(), KUcur()));
+    LST(apply(LREP_OP_M, d, Vcur(), MVcur()));
+    stale = false;
+    return LREP_OK;
+  }
+
+  // ----------------------------------------- Step 3 + Step 4 (one pass)
+  // Grams, small LREP, pullback of Ritz pairs [0, e) into the next buffer
+  // and their residuals; reads back lam, eps, info and the biorth error.
+  lrep_status rayleigh_ritz(int e) {
+    const Segs sU = seg1(Ucur(), ld, d), sV = seg1(Vcur(), ld, d);
+    const Segs sKU = seg1(KUcur(), ld, d), sMV = seg1(MVcur(), ld, d);
+    if (events) LCK(cudaEventRecord(ev[0], st));
+    LST(gram(sU, sKU, Kh, dmax));
+    LST(gram(sV, sMV, Mh, dmax));
+    LST(gram(sU, sV, Sh, dmax));
+    SmallJob job{};
+    job.Khat = Kh; job.Mhat = Mh; job.ld_in = dmax; job.S = Sh;
+    job.lam = lam_d; job.Xh = Xh; job.Yh = Yh; job.ldo = dmax;
+    job.work = swork; job.info = info_d; job.biorth_err = berr_d;
+    job.d = d; job.w_prev = w_prev;
+    LCK(small_lrep_one(job, st));
+    const int t = nx();
+    LST(update(e, 0.0, sU, Xh, dmax, 1.0, UX[t]));
+    LST(update(e, 0.0, sV, Yh, dmax, 1.0, UY[t]));
+    LST(update(e, 0.0, sKU, Xh, dmax, 1.0, KX[t]));
+    LST(update(e, 0.0, sMV, Yh, dmax, 1.0, MY[t]));
+    if (events) LCK(cudaEventRecord(ev[1], st));
+    LCK(residuals_f64(n, e, UX[t], UY[t], KX[t], MY[t], ld, lam_d, eps_d, part,
+                      counters, st));
+    LCK(cudaMemcpyAsync(h->lam, lam_d, sizeof(double) * d, cudaMemcpyDeviceToHost, st));
+    LCK(cudaMemcpyAsync(h->eps, eps_d, sizeof(double) * e, cudaMemcpyDeviceToHost, st));
+    LCK(cudaMemcpyAsync(&h->berr, berr_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LCK(cudaMemcpyAsync(&h->info, info_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (events) LCK(cudaEventRecord(ev[2], st));
+    LST(sync());
+    if (h->info == 1 || h->info == 2)
+      return p->fail(LREP_ERR_NOT_SPD,
+                     h->info == 1 ? "projected K^ = U^T K U is not positive definite "
+                                    "(is K singular without a nullspace basis?)"
+                                  : "projected M^ = V^T M V is not positive definite");
+    for (int i = 0; i < e; ++i)
+      if (!std::isfinite(h->eps[i]) || !std::isfinite(h->lam[i]))
+        return p->fail(LREP_ERR_BREAKDOWN, "non-finite Ritz value or residual");
+    return LREP_OK;
+  }
+
+  // safeguard: Step 2's biorthogonalisation applied to the current U, V;
+  // K U and M V follow by the same combinations.
+  lrep_status rebiorth() {
+    const int t = nx();
+    int kept = 0;
+    LST(biorth_block(Ucur(), Vcur(), d, KUcur(), MVcur(), UX[t], UY[t], KX[t], MY[t],
+                     UX[cur], UY[cur], KX[cur], MY[cur], nullptr, nullptr, &kept));
+    if (kept == 0) return p->fail(LREP_ERR_BREAKDOWN, "re-biorthogonalisation lost every column");
+    off = 0;
+    d = kept;
+    p->rebiorths++;
+    return LREP_OK;
+  }
+
+  lrep_status lock(int first, int count) {
+    const int t = nx();
+    LCK(copy_cols(n, count, UX[t] + (int64_t)first * ld, ld, Dx + (int64_t)(r + ell) * ld, ld, st));
+    LCK(copy_cols(n, count, UY[t] + (int64_t)first * ld, ld, Dy + (int64_t)(r + ell) * ld, ld, st));
+    for (int i = 0; i < count; ++i) locked.push_back(h->lam[first + i]);
+    ell += count;
+    return LREP_OK;
+  }
+
+  // ------------------------------------------------------------- solve
+  lrep_status run() {
+    auto t0 = std::chrono::steady_clock::now();
+    LST(setup());
+    LST(sync());
+    p->timings[0] += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const int maxit = p->opts.maxit;
+    const int every = std::max(1, p->opts.refresh_every);
+    bool converged = false;
+    int it = 0;
+    for (it = 1; it <= maxit; ++it) {
+      if (it > 1 && it % every == 0) LST(refresh());
+      const int want_max = std::min(w, d);
+      int e = std::min(d, want_max + (moving ? 2 * nb : 0));
+      LST(rayleigh_ritz(e));
+      if (h->berr > p->opts.rebiorth_tol) {
+        LST(rebiorth());
+        LST(refresh());
+        e = std::min(d, std::min(w, d) + (moving ? 2 * nb : 0));
+        LST(rayleigh_ritz(e));
+      }
+      int wv = std::min(w, d);
+      int want = std::min(wv, nev - ell);
+      int c = 0;
+      while (c < wv && h->eps[c] < tol) ++c;
+      const bool decide = (c >= want) || (moving && c >= 2 * nb);
+      if (decide && stale) {
+        // decisions are taken on freshly computed products
+        LST(refresh());
+        e = std::min(d, std::min(w, d) + (moving ? 2 * nb : 0));
+        LST(rayleigh_ritz(e));
+        wv = std::min(w, d);
+        want = std::min(wv, nev - ell);
+        c = 0;
+        while (c < wv && h->eps[c] < tol) ++c;
+      }
+      double emax = 0.0;
+      for (int i = 0; i < std::min(wv, want); ++i) emax = std::max(emax, h->eps[i]);
+      p->history.push_back(emax);
+      if (p->opts.verbose)
+        fprintf(stderr, "[lrep] it %d d %d locked %d conv %d/%d maxres %.3e lam0 %.12e\n",
+                it, d, ell, c, want, emax, h->lam[0]);
+      if (c >= want) {
+        LST(lock(0, want));
+        converged = true;
+        break;
+      }
+      int win0 = 0;
+      if (moving && c >= 2 * nb) {
+        LST(lock(0, 2 * nb));
+        win0 = 2 * nb;
+        wv = std::min(w, d - win0);
+      }
+      const int end = win0 + wv;
+      // active set: the first nb unconverged pairs of the window
+      int na = 0;
+      for (int j = win0; j < end && na < nb; ++j)
+        if (!(h->eps[j] < tol)) {
+          h->act[na] = j;
+          h->lam_act[na] = h->lam[j];
+          ++na;
+        }
+      if (na == 0) {  // everything in the window converged but not locked
+        LST(lock(win0, std::min(wv, nev - ell)));
+        converged = ell >= nev;
+        if (converged) break;
+        continue;
+      }
+      LCK(cudaMemcpyAsync(act_d, h->act, sizeof(int) * na, cudaMemcpyHostToDevice, st));
+      LCK(cudaMemcpyAsync(lam_act, h->lam_act, sizeof(double) * na, cudaMemcpyHostToDevice, st));
+      LST(step5_6_7(win0, wv, end, na));
+      if (d == 0) return p->fail(LREP_ERR_BREAKDOWN, "search space collapsed");
+    }
+    p->iters = std::min(it, maxit);
+    LST(finalize());
+    if (events) {
+      // nothing: phase times were accumulated per iteration
+    }
+    return converged ? LREP_OK : LREP_NOT_CONVERGED;
+  }
+
+  lrep_status step5_6_7(int win0, int wv, int end, int na) {
+    const int t = nx();
+    double* TX = UX[t];
+    double* TY = UY[t];
+    double* TK = KX[t];
+    double* TM = MY[t];
+    // Step 5: eq. hat_pq in R^d and Alg. 1 there (P is empty after a move)
+    const bool with_p = (win0 == 0);
+    if (with_p) {
+      PqJob pj{};
+      pj.Xh = Xh; pj.Yh = Yh; pj.ld = dmax; pj.d = d; pj.end = end;
+      pj.w_prev = w_prev; pj.na = na; pj.act = act_d; pj.Ph = Ph; pj.Qh = Qh;
+      pj.ldo = dmax; pj.work = pqwork; pj.count = cnt_d + 1; pj.tau = p->opts.discard_tol;
+      LCK(small_pq(pj, st));
+      LCK(cudaMemcpyAsync(&h->cnt[1], cnt_d + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    } else {
+      h->cnt[1] = 0;
+    }
+    cudaEvent_t evp = ev[5];
+    if (events) LCK(cudaEventRecord(ev[3], st));
+    LCK(cudaEventRecord(evp, st));
+    // Step 6: eq. block_GS, one CG per column, W^(0) = 0
+    const bool cgop = true;
+    double* Wsol = Wr;
+    double* Zsol = Zr;
+    for (int sweep = 0; sweep < std::max(1, p->opts.ngs); ++sweep) {
+      // M Z = W Lambda + (X~ Lambda - M Y~)
+      LCK(gather_combine(n, na, act_d, lam_act, TX, -1.0, TM, sweep ? lam_act : nullptr,
+                         sweep ? Wsol : nullptr, ld, Rhs, ld, st));
+      LST(cg_solve(LREP_OP_M, na, Rhs, Zsol, p->opts.cg_tol, p->opts.cg_maxit, 0, cgop));
+      // K W = Z Lambda + (Y~ Lambda - K X~), projected onto range(K)
+      LCK(gather_combine(n, na, act_d, lam_act, TY, -1.0, TK, lam_act, Zsol, ld, Rhs, ld, st));
+      if (r > 0) {
+        LST(gram(seg1(Q0, ld, r), seg1(Rhs, ld, na), Cproj, r));
+        LST(update(na, 1.0, seg1(Q0, ld, r), Cproj, r, -1.0, Rhs));
+      }
+      LST(cg_solve(LREP_OP_K, na, Rhs, Wsol, p->opts.cg_tol, p->opts.cg_maxit, 0, cgop));
+    }
+    // entering norms for the discard rule
+    LCK(colnorm2_f64(n, na, Wsol, ld, refw2, part, counters + 1, st));
+    LCK(colnorm2_f64(n, na, Zsol, ld, refz2, part, counters + 1, st));
+    // P~ = U P^, Q~ = V Q^ and their products by the same combinations
+    LCK(cudaEventSynchronize(evp));
+    const int pc = h->cnt[1];
+    const Segs sU = seg1(Ucur(), ld, d), sV = seg1(Vcur(), ld, d);
+    const Segs sKU = seg1(KUcur(), ld, d), sMV = seg1(MVcur(), ld, d);
+    if (pc > 0) {
+      LST(update(pc, 0.0, sU, Ph, dmax, 1.0, TX + (int64_t)end * ld));
+      LST(update(pc, 0.0, sV, Qh, dmax, 1.0, TY + (int64_t)end * ld));
+      LST(update(pc, 0.0, sKU, Ph, dmax, 1.0, TK + (int64_t)end * ld));
+      LST(update(pc, 0.0, sMV, Qh, dmax, 1.0, TM + (int64_t)end * ld));
+    }
+    // eq. update_W / update_Z against [X0, X_locked, X~, P~] (applied twice)
+    const int nw = wv + pc;
+    const Segs SA = seg_push(seg1(Dx, ld, r + ell), TX + (int64_t)win0 * ld, ld, nw);
+    const Segs SB = seg_push(seg1(Dy, ld, r + ell), TY + (int64_t)win0 * ld, ld, nw);
+    const int L = r + ell + nw;
+    for (int pass = 0; pass < 2; ++pass) {
+      LST(gram(SB, seg1(Wsol, ld, na), Cproj, L));
+      LST(update(na, 1.0, SA, Cproj, L, -1.0, Wsol));
+      LST(gram(SA, seg1(Zsol, ld, na), Cproj, L));
+      LST(update(na, 1.0, SB, Cproj, L, -1.0, Zsol));
+    }
+    // Alg. 1 on (W~, Z~) with the discard rule, into place after P~
+    const int wpos = end + pc;
+    int m = 0;
+    LST(biorth_block(Wsol, Zsol, na, nullptr, nullptr, TW, TZ, nullptr, nullptr,
+                     TX + (int64_t)wpos * ld, TY + (int64_t)wpos * ld, nullptr, nullptr,
+                     refw2, refz2, &m));
+    // fresh products K W~, M Z~
+    LST(apply(LREP_OP_K, m, TX + (int64_t)wpos * ld, TK + (int64_t)wpos * ld));
+    LST(apply(LREP_OP_M, m, TY + (int64_t)wpos * ld, TM + (int64_t)wpos * ld));
+    if (events) LCK(cudaEventRecord(ev[4], st));
+    LST(sync());
+    if (events) {
+      float a = 0, b = 0, c2 = 0, e2 = 0;
+      cudaEventElapsedTime(&a, ev[0], ev[1]);
+      cudaEventElapsedTime(&b, ev[1], ev[2]);
+      cudaEventElapsedTime(&c2, ev[2], ev[3]);
+      cudaEventElapsedTime(&e2, ev[3], ev[4]);
+      p->timings[1] += a * 1e-3; p->timings[2] += b * 1e-3;
+      p->timings[3] += c2 * 1e-3; p->timings[4] += e2 * 1e-3;
+    }
+    // Step 7: U = [X~, P~, W~], V = [Y~, Q~, Z~]
+    cur = t;
+    off = win0;
+    d = wv + pc + m;
+    w_prev = wv;
+    stale = true;
+    return LREP_OK;
+  }
+
+  lrep_status finalize() {
+    const int nc = ell;
+    p->nconv = nc;
+    p->lam = locked;
+    p->Xres = Dx + (int64_t)r * ld;
+    p->Yres = Dy + (int64_t)r * ld;
+    p->res_ld = ld;
+    p->resid.assign(nc, 0.0);
+    p->biorth_err = 0.0;
+    if (nc == 0) return LREP_OK;
+    LCK(fix_sign(n, nc, p->Xres, p->Yres, ld, st));
+    LCK(cudaMemcpyAsync(lam_lock, locked.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st));
+    // final residuals with fresh float64 products (eq. tol)
+    for (int c0 = 0; c0 < nc; c0 += C) {
+      const int cc = std::min(C, nc - c0);
+      double* X = p->Xres + (int64_t)c0 * ld;
+      double* Y = p->Yres + (int64_t)c0 * ld;
+      LST(apply(LREP_OP_K, cc, X, KX[0]));
+      LST(apply(LREP_OP_M, cc, Y, MY[0]));
+      LCK(residuals_f64(n, cc, X, Y, KX[0], MY[0], ld, lam_lock + c0, eps_d, part,
+                        counters, st));
+      LCK(cudaMemcpyAsync(h->eps, eps_d, sizeof(double) * cc, cudaMemcpyDeviceToHost, st));
+      LST(sync());
+      for (int i = 0; i < cc; ++i) p->resid[c0 + i] = h->eps[i];
+    }
+    // biorthogonality of the result
+    if (nc <= 512) {
+      double* G = (2 * dmax * 2 * dmax >= nc * nc) ? G2 : nullptr;
+      if (G) {
+        LST(gram(seg1(p->Xres, ld, nc), seg1(p->Yres, ld, nc), G, nc));
+        LCK(biorth_error(nc, G, nc, berr_d, st));
+        LCK(cudaMemcpyAsync(&h->berr, berr_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+        LST(sync());
+        p->biorth_err = h->berr;
+      }
+    }
+    return LREP_OK;
+  }
+};
+
+}  // namespace
+
+lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol) {
+  Solver S{};
+  S.p = p;
+  S.st = p->stream;
+  S.n = p->op.n;
+  S.r = p->r;
+  S.nev = nev;
+  S.nb = std::min(nb, nev);
+  S.moving = S.nb < nev;
+  S.w = (int)std::min<int64_t>(S.moving ? (int64_t)p->opts.s * S.nb : nev, S.n - S.r);
+  S.dmax = S.w + 2 * S.nb;
+  S.C = S.w + 4 * S.nb;
+  S.Lmax = S.r + nev + S.dmax;
+  S.tol = tol;
+  for (double& v : p->prof) v = 0.0;
+  if (S.dmax > 256) return p->fail(LREP_ERR_ARG, "window + 2*block exceeds 256 columns");
+  if (S.nb > 64) return p->fail(LREP_ERR_ARG, "block exceeds 64");
+  if ((int64_t)S.dmax > S.n - S.r) return p->fail(LREP_ERR_ARG, "n too small for nev/block");
+  p->history.clear();
+  p->iters = 0;
+  p->matvecs = 0;
+  p->rebiorths = 0;
+  for (double& t : p->timings) t = 0.0;
+  lrep_status s = S.alloc();
+  if (s == LREP_OK) {
+    S.events = true;
+    for (auto& e : S.ev)
+      if (cudaEventCreate(&e) != cudaSuccess) S.events = false;
+    s = S.run();
+  }
+  S.release_host();
+  p->solved = (s == LREP_OK || s == LREP_NOT_CONVERGED);
+  p->nev_solved = nev;
+  return s;
+}
+
+}  // namespace lrep

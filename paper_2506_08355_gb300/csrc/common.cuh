@@ -1,0 +1,103 @@
+// Internal helpers shared by the CUDA translation units of the solver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cstdio>
+
+namespace lrep {
+
+// kernels launched by this library since load (lrep_launch_count)
+extern std::atomic<long long> g_launches;
+#define LREP_COUNT_LAUNCH() (::lrep::g_launches.fetch_add(1, std::memory_order_relaxed))
+
+constexpr int kNumSMs = 152;          // GB300: 2 dies x 76 SMs
+constexpr int kMaxSegs = 3;           // column segments of one logical block
+
+// A logical n x (sum cols) block made of up to kMaxSegs column-major
+// pieces (e.g. [X0 | X_locked] next to [X~ | P~]).
+struct Segs {
+  const double* ptr[kMaxSegs];
+  int64_t ld[kMaxSegs];
+  int cols[kMaxSegs];
+  int nseg;
+  __host__ __device__ int total() const {
+    int t = 0;
+    for (int s = 0; s < nseg; ++s) t += cols[s];
+    return t;
+  }
+  __host__ __device__ const double* col(int j) const {
+    for (int s = 0; s < nseg; ++s) {
+      if (j < cols[s]) return ptr[s] + (int64_t)j * ld[s];
+      j -= cols[s];
+    }
+    return nullptr;
+  }
+};
+
+inline Segs seg1(const double* p, int64_t ld, int cols) {
+  Segs s{};
+  s.ptr[0] = p; s.ld[0] = ld; s.cols[0] = cols; s.nseg = 1;
+  return s;
+}
+inline Segs seg_push(Segs s, const double* p, int64_t ld, int cols) {
+  if (cols <= 0) return s;
+  s.ptr[s.nseg] = p; s.ld[s.nseg] = ld; s.cols[s.nseg] = cols; s.nseg++;
+  return s;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum for blockDim.x a multiple of 32 (<= 1024); every thread
+// receives the result.  `red` must hold 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  t = red[0];
+  __syncthreads();
+  return t;
+}
+
+// "Last block done" handshake for two-stage reductions with a fixed
+// summation order: every block writes its partials, then the last block to
+// arrive reduces them in index order and resets the counter for the next
+// launch.  Returns true in the last block.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
+    last = (atomicAdd(counter, 1u) == nblk - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) *counter = 0u;
+  return last;
+}
+
+// Read through L2 (partials written by other blocks of the same launch).
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+
+// Number of row slabs used by the fixed-order reductions over n rows.
+inline int reduction_slabs(int64_t n, int rows_per_slab_min = 512, int max_slabs = 2 * kNumSMs) {
+  int64_t s = (n + rows_per_slab_min - 1) / rows_per_slab_min;
+  if (s < 1) s = 1;
+  if (s > max_slabs) s = max_slabs;
+  return (int)s;
+}
+
+}  // namespace lrep

@@ -1,0 +1,255 @@
+// Matrix-free operator products (7-point stencil, CSR) and the vector
+// kernels of the block CG used for eq. block_GS (one independent CG per
+// column; per-column alpha, beta; columns stop when ||r|| <= tol ||b||).
+//
+// CG control stays on the device: each kernel reads the `done` flag and
+// returns at once when every column has converged, so the host can
+// enqueue the iteration budget without a read-back per step.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lrep {
+namespace {
+
+// ------------------------------------------------------------- stencil
+// Y = coef * Lap_h X + d .* X, zero values outside the grid.  One thread per
+// grid point, blockIdx.y = column; x-neighbours are coalesced, y/z
+// neighbours come from L1/L2 (the planes of a column stay cache-resident).
+__global__ void __launch_bounds__(256)
+stencil_kernel(int nx, int ny, int nz, double coef, const double* __restrict__ d,
+               const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
+               int64_t ldy, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t plane = (int64_t)nx * ny;
+  const double* x = X + (int64_t)blockIdx.y * ldx;
+  double* y = Y + (int64_t)blockIdx.y * ldy;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(p % nx);
+    const int j = (int)((p / nx) % ny);
+    const int k = (int)(p / plane);
+    const double c = x[p];
+    double s = -6.0 * c;
+    if (i > 0) s += x[p - 1];
+    if (i < nx - 1) s += x[p + 1];
+    if (j > 0) s += x[p - nx];
+    if (j < ny - 1) s += x[p + nx];
+    if (k > 0) s += x[p - plane];
+    if (k < nz - 1) s += x[p + plane];
+    y[p] = fma(coef, s, d[p] * c);
+  }
+}
+
+// ----------------------------------------------------------------- CSR
+// One thread per row; the row's entries are read once and applied to up to
+// 8 columns per pass.
+__global__ void __launch_bounds__(256)
+csr_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+           const double* __restrict__ v, int c, const double* __restrict__ X,
+           int64_t ldx, double* __restrict__ Y, int64_t ldy,
+           const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = rp[row], e = rp[row + 1];
+    for (int c0 = 0; c0 < c; c0 += 8) {
+      double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      const int cw = min(8, c - c0);
+      for (int64_t q = b; q < e; ++q) {
+        const int64_t col = ci[q];
+        const double a = v[q];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (t < cw) acc[t] = fma(a, X[col + (int64_t)(c0 + t) * ldx], acc[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t < cw) Y[row + (int64_t)(c0 + t) * ldy] = acc[t];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ CG
+__global__ void __launch_bounds__(256)
+cg_init_kernel(int64_t n, int nb, const double* __restrict__ B, int64_t ldb,
+               double* __restrict__ X, double* __restrict__ R, double* __restrict__ P,
+               int64_t ld, double tol, CgState s, int64_t slab_rows) {
+  __shared__ double red[32];
+  const int col = blockIdx.y, slab = blockIdx.x, slabs = gridDim.x;
+  const int64_t r0 = (int64_t)slab * slab_rows, r1 = min(n, r0 + slab_rows);
+  double acc = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const double b = B[i + (int64_t)col * ldb];
+    X[i + (int64_t)col * ld] = 0.0;
+    R[i + (int64_t)col * ld] = b;
+    P[i + (int64_t)col * ld] = b;
+    acc = fma(b, b, acc);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) s.part[(int64_t)col * slabs + slab] = acc;
+  if (!arrive_last(s.counter + 2)) return;
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+    double rho = 0.0;
+    for (int z = 0; z < slabs; ++z) rho += ld_cg(s.part + (int64_t)c * slabs + z);
+    s.rho[c] = rho;
+    s.stop[c] = tol * tol * rho;
+    const int act = (rho > tol * tol * rho) && isfinite(rho);
+    s.active[c] = act;
+    s.alpha[c] = 0.0;
+    s.beta[c] = 0.0;
+    if (act) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *s.done = any ? 0 : 1;
+}
+
+__global__ void __launch_bounds__(256)
+cg_alpha_kernel(int64_t n, int nb, const double* __restrict__ P,
+                const double* __restrict__ Q, int64_t ld, CgState s, int64_t slab_rows) {
+  if (*s.done) return;
+  __shared__ double red[32];
+  const int col = blockIdx.y, slab = blockIdx.x, slabs = gridDim.x;
+  const int64_t r0 = (int64_t)slab * slab_rows, r1 = min(n, r0 + slab_rows);
+  double acc = 0.0;
+  if (s.active[col])
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x)
+      acc = fma(P[i + (int64_t)col * ld], Q[i + (int64_t)col * ld], acc);
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) s.part[(int64_t)col * slabs + slab] = acc;
+  if (!arrive_last(s.counter)) return;
+  if (threadIdx.x == 0 && s.iters) *s.iters += 1;
+  for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+    double pq = 0.0;
+    for (int z = 0; z < slabs; ++z) pq += ld_cg(s.part + (int64_t)c * slabs + z);
+    if (s.active[c] && pq > 0.0 && isfinite(pq)) {
+      s.alpha[c] = s.rho[c] / pq;
+    } else {
+      s.alpha[c] = 0.0;
+      s.active[c] = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+cg_update_kernel(int64_t n, int nb, double* __restrict__ X, double* __restrict__ R,
+                 const double* __restrict__ P, const double* __restrict__ Q,
+                 int64_t ld, CgState s, int64_t slab_rows) {
+  if (*s.done) return;
+  __shared__ double red[32];
+  const int col = blockIdx.y, slab = blockIdx.x, slabs = gridDim.x;
+  const int64_t r0 = (int64_t)slab * slab_rows, r1 = min(n, r0 + slab_rows);
+  const double a = s.alpha[col];
+  double acc = 0.0;
+  if (a != 0.0)
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const int64_t o = i + (int64_t)col * ld;
+      X[o] = fma(a, P[o], X[o]);
+      const double r = fma(-a, Q[o], R[o]);
+      R[o] = r;
+      acc = fma(r, r, acc);
+    }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) s.part[(int64_t)col * slabs + slab] = acc;
+  if (!arrive_last(s.counter + 1)) return;
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+    if (s.active[c]) {
+      double rn = 0.0;
+      for (int z = 0; z < slabs; ++z) rn += ld_cg(s.part + (int64_t)c * slabs + z);
+      s.beta[c] = rn / s.rho[c];
+      s.rho[c] = rn;
+      if (!(rn > s.stop[c]) || !isfinite(rn)) s.active[c] = 0;
+    }
+    if (s.active[c]) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *s.done = any ? 0 : 1;
+}
+
+__global__ void cg_pdir_kernel(int64_t n, const double* __restrict__ R,
+                               double* __restrict__ P, int64_t ld, CgState s) {
+  if (*s.done) return;
+  const int col = blockIdx.y;
+  if (!s.active[col]) return;
+  const double b = s.beta[col];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = i + (int64_t)col * ld;
+    P[o] = fma(b, P[o], R[o]);
+  }
+}
+
+int cg_slabs(int64_t n) { return reduction_slabs(n, 2048, 64); }
+unsigned grid_rows(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2 * kNumSMs));
+}
+}  // namespace
+
+cudaError_t stencil_apply_f64(int nx, int ny, int nz, double coef_h2,
+                              const double* d, int c, const double* X,
+                              int64_t ldx, double* Y, int64_t ldy,
+                              const int* skip, cudaStream_t st) {
+  if (c <= 0) return cudaSuccess;
+  const int64_t n = (int64_t)nx * ny * nz;
+  const unsigned gx = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((n + 255) / 256, 8 * kNumSMs));
+  stencil_kernel<<<dim3(gx, c), 256, 0, st>>>(nx, ny, nz, coef_h2, d, X, ldx, Y,
+                                             ldy, skip); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t csr_apply_f64(int64_t n, const int64_t* rp, const int32_t* ci,
+                          const double* v, int c, const double* X, int64_t ldx,
+                          double* Y, int64_t ldy, const int* skip,
+                          cudaStream_t st) {
+  if (c <= 0) return cudaSuccess;
+  const unsigned gx = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((n + 255) / 256, 8 * kNumSMs));
+  csr_kernel<<<gx, 256, 0, st>>>(n, rp, ci, v, c, X, ldx, Y, ldy, skip); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+size_t cg_part_elems(int64_t n, int nb) { return (size_t)cg_slabs(n) * nb; }
+
+cudaError_t cg_init(int64_t n, int nb, const double* B, int64_t ldb, double* X,
+                    double* R, double* P, int64_t ld, double tol, CgState& s,
+                    cudaStream_t st) {
+  const int slabs = cg_slabs(n);
+  s.slabs = slabs;
+  const int64_t sr = (n + slabs - 1) / slabs;
+  cg_init_kernel<<<dim3(slabs, nb), 256, 0, st>>>(n, nb, B, ldb, X, R, P, ld, tol, s, sr); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t cg_alpha(int64_t n, int nb, const double* P, const double* Q,
+                     int64_t ld, CgState& s, cudaStream_t st) {
+  const int64_t sr = (n + s.slabs - 1) / s.slabs;
+  cg_alpha_kernel<<<dim3(s.slabs, nb), 256, 0, st>>>(n, nb, P, Q, ld, s, sr); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t cg_update(int64_t n, int nb, double* X, double* R, const double* P,
+                      const double* Q, int64_t ld, CgState& s, cudaStream_t st) {
+  const int64_t sr = (n + s.slabs - 1) / s.slabs;
+  cg_update_kernel<<<dim3(s.slabs, nb), 256, 0, st>>>(n, nb, X, R, P, Q, ld, s, sr); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t cg_pdir(int64_t n, int nb, const double* R, double* P, int64_t ld,
+                    CgState& s, cudaStream_t st) {
+  cg_pdir_kernel<<<dim3(grid_rows(n), nb), 256, 0, st>>>(n, R, P, ld, s); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+}  // namespace lrep

@@ -1,0 +1,480 @@
+// Small dense steps of one BOSP iteration, one CTA per problem:
+//  * the projected LREP of eq. small_eigen by two Cholesky factorisations
+//    and one SVD (Section 3.3, cost item 2), the SVD by one-sided
+//    (Hestenes) Jacobi with a round-robin pair order;
+//  * P^, Q^ of eq. hat_pq followed by Alg. 1 in R^d;
+//  * Alg. 1 for a large n x m pair (W, Z) carried out on the Gram
+//    matrices of [W Z]: the coefficient vectors a_l, b_l with p_l = W a_l,
+//    q_l = Z b_l follow Alg. 1's updates exactly, inner products
+//    q_j^T p = (Z b_j)^T W a being read from the Grams.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lrep {
+namespace {
+
+constexpr int SMALL_T = 512;
+constexpr int SMALL_MAXD = 256;
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    red[0] = t;
+  }
+  __syncthreads();
+  t = red[0];
+  __syncthreads();
+  return t;
+}
+
+// In-place lower Cholesky of a d x d column-major matrix (ld = d); returns
+// false (uniformly) when a pivot is not positive and finite.
+__device__ bool chol_lower(double* L, int d, int* s_flag) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = 0; j < d; ++j) {
+    if (tid == 0) {
+      const double v = L[j + j * d];
+      if (!(v > 0.0) || !isfinite(v)) *s_flag = 1;
+      else L[j + j * d] = sqrt(v);
+    }
+    __syncthreads();
+    if (*s_flag) return false;
+    const double piv = L[j + j * d];
+    for (int i = j + 1 + tid; i < d; i += nt) L[i + j * d] /= piv;
+    __syncthreads();
+    const int m = d - j - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int ii = e % m, kk = e / m;
+      if (ii < kk) continue;
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      L[i + k * d] -= L[i + j * d] * L[k + j * d];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < d * d; e += nt) {
+    const int i = e % d, k = e / d;
+    if (i < k) L[e] = 0.0;
+  }
+  __syncthreads();
+  return true;
+}
+
+__device__ void small_lrep_body(const SmallJob& J) {
+  const int d = J.d;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  __shared__ int s_flag;
+  __shared__ int s_conv;
+  __shared__ double red[32];
+  __shared__ double sig[SMALL_MAXD];
+  __shared__ int perm[SMALL_MAXD];
+  __shared__ int flip[SMALL_MAXD];
+  double* L1 = J.work;
+  double* L2 = L1 + (size_t)d * d;
+  double* G = L2 + (size_t)d * d;
+  double* V = G + (size_t)d * d;
+  if (tid == 0) s_flag = 0;
+  // biorthogonality of the current basis (safeguard input)
+  if (J.S) {
+    double m = 0.0;
+    for (int e = tid; e < d * d; e += nt) {
+      const int i = e % d, j = e / d;
+      m = fmax(m, fabs(J.S[i + (size_t)j * J.ld_in] - (i == j ? 1.0 : 0.0)));
+    }
+    m = block_max(m, red);
+    if (tid == 0) *J.biorth_err = m;
+  }
+  for (int e = tid; e < d * d; e += nt) {
+    const int i = e % d, j = e / d;
+    L1[e] = 0.5 * (J.Khat[i + (size_t)j * J.ld_in] + J.Khat[j + (size_t)i * J.ld_in]);
+    L2[e] = 0.5 * (J.Mhat[i + (size_t)j * J.ld_in] + J.Mhat[j + (size_t)i * J.ld_in]);
+  }
+  __syncthreads();
+  if (!chol_lower(L1, d, &s_flag)) {
+    if (tid == 0) *J.info = 1;
+    return;
+  }
+  if (!chol_lower(L2, d, &s_flag)) {
+    if (tid == 0) *J.info = 2;
+    return;
+  }
+  // G = L1^T L2 (both lower triangular), V = I
+  for (int e = tid; e < d * d; e += nt) {
+    const int i = e % d, j = e / d;
+    double s = 0.0;
+    for (int k = max(i, j); k < d; ++k) s = fma(L1[k + i * d], L2[k + j * d], s);
+    G[e] = s;
+    V[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // one-sided Jacobi on the columns of G (G V -> W S)
+  const int dp = d + (d & 1), m = dp - 1;
+  const double tol = 4.0 * 2.220446049250313e-16 * sqrt((double)d);
+  int converged = 0;
+  for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
+    if (tid == 0) s_conv = 1;
+    __syncthreads();
+    for (int r = 0; r < m; ++r) {
+      for (int p = wid; p < dp / 2; p += nw) {
+        int a, b;
+        if (p == 0) { a = r; b = m; }
+        else { a = (r + p) % m; b = (r - p + m) % m; }
+        if (a > b) { const int t = a; a = b; b = t; }
+        if (b >= d) continue;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < d; i += 32) {
+          const double x = G[i + a * d], y = G[i + b * d];
+          al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (fabs(ga) > tol * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          for (int i = lane; i < d; i += 32) {
+            const double x = G[i + a * d], y = G[i + b * d];
+            G[i + a * d] = c * x - s * y;
+            G[i + b * d] = s * x + c * y;
+            const double u = V[i + a * d], v = V[i + b * d];
+            V[i + a * d] = c * u - s * v;
+            V[i + b * d] = s * u + c * v;
+          }
+          if (lane == 0) s_conv = 0;
+        }
+      }
+      __syncthreads();
+    }
+    converged = s_conv;
+    __syncthreads();
+  }
+  // singular values, ascending order (ties by index)
+  for (int j = wid; j < d; j += nw) {
+    double s = 0.0;
+    for (int i = lane; i < d; i += 32) s = fma(G[i + j * d], G[i + j * d], s);
+    s = warp_sum(s);
+    if (lane == 0) sig[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = tid; j < d; j += nt) {
+    int rk = 0;
+    for (int k = 0; k < d; ++k) rk += (sig[k] < sig[j]) || (sig[k] == sig[j] && k < j);
+    perm[rk] = j;
+  }
+  __syncthreads();
+  // X^ = L2 V S^-1/2,  Y^ = L1 W S^-1/2 with W = G V / S (G holds G V)
+  for (int e = tid; e < d * d; e += nt) {
+    const int r = e % d, i = e / d;
+    const int j = perm[i];
+    const double s = sig[j];
+    double x = 0.0, y = 0.0;
+    for (int k = 0; k <= r; ++k) {
+      x = fma(L2[r + k * d], V[k + j * d], x);
+      y = fma(L1[r + k * d], G[k + j * d], y);
+    }
+    J.Xh[r + (size_t)i * J.ldo] = x / sqrt(s);
+    J.Yh[r + (size_t)i * J.ldo] = y / (s * sqrt(s));
+  }
+  for (int i = tid; i < d; i += nt) J.lam[i] = sig[perm[i]];
+  __syncthreads();
+  // sign of each Ritz pair follows its previous iterate (X^[j, j] >= 0)
+  const int wa = min(J.w_prev, d);
+  for (int j = tid; j < d; j += nt) flip[j] = (j < wa) && (J.Xh[j + (size_t)j * J.ldo] < 0.0);
+  __syncthreads();
+  for (int e = tid; e < d * d; e += nt) {
+    const int r = e % d, i = e / d;
+    if (flip[i]) {
+      J.Xh[r + (size_t)i * J.ldo] = -J.Xh[r + (size_t)i * J.ldo];
+      J.Yh[r + (size_t)i * J.ldo] = -J.Yh[r + (size_t)i * J.ldo];
+    }
+  }
+  if (tid == 0) *J.info = converged ? 0 : 3;
+}
+
+__global__ void __launch_bounds__(SMALL_T) small_lrep_kernel(const SmallJob* __restrict__ jobs) {
+  const SmallJob J = jobs[blockIdx.x];
+  small_lrep_body(J);
+}
+
+__global__ void __launch_bounds__(SMALL_T) small_lrep_one_kernel(SmallJob J) {
+  small_lrep_body(J);
+}
+
+// ---------------------------------------------------------------- eq. hat_pq
+__global__ void __launch_bounds__(256) small_pq_kernel(PqJob J) {
+  const int d = J.d, na = J.na, end = J.end;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* Pa = J.work;                 // d x na
+  double* Qa = Pa + (size_t)d * na;
+  double* T = Qa + (size_t)d * na;     // end x na coefficients (2 blocks)
+  double* T2 = T + (size_t)d * na;
+  __shared__ double refp[64], refq[64];
+  // entering vectors X^_j - E_j, Y^_j - E_j
+  for (int e = tid; e < d * na; e += nt) {
+    const int r = e % d, c = e / d;
+    const int j = J.act[c];
+    const double ej = (j < J.w_prev && r == j) ? 1.0 : 0.0;
+    Pa[e] = J.Xh[r + (size_t)j * J.ld] - ej;
+    Qa[e] = J.Yh[r + (size_t)j * J.ld] - ej;
+  }
+  __syncthreads();
+  for (int c = tid; c < na; c += nt) {
+    double sp = 0.0, sq = 0.0;
+    for (int r = 0; r < d; ++r) {
+      sp = fma(Pa[r + c * d], Pa[r + c * d], sp);
+      sq = fma(Qa[r + c * d], Qa[r + c * d], sq);
+    }
+    refp[c] = sqrt(sp);
+    refq[c] = sqrt(sq);
+  }
+  // T = Y^[:, :end]^T Pa, T2 = X^[:, :end]^T Qa
+  for (int e = tid; e < end * na; e += nt) {
+    const int k = e % end, c = e / end;
+    double s = 0.0, s2 = 0.0;
+    for (int r = 0; r < d; ++r) {
+      s = fma(J.Yh[r + (size_t)k * J.ld], Pa[r + c * d], s);
+      s2 = fma(J.Xh[r + (size_t)k * J.ld], Qa[r + c * d], s2);
+    }
+    T[k + c * end] = s;
+    T2[k + c * end] = s2;
+  }
+  __syncthreads();
+  // projected: P^ = Pa - X^ T, Q^ = Qa - Y^ T2 (written to the outputs)
+  for (int e = tid; e < d * na; e += nt) {
+    const int r = e % d, c = e / d;
+    double p = Pa[e], q = Qa[e];
+    for (int k = 0; k < end; ++k) {
+      p = fma(-J.Xh[r + (size_t)k * J.ld], T[k + c * end], p);
+      q = fma(-J.Yh[r + (size_t)k * J.ld], T2[k + c * end], q);
+    }
+    J.Ph[r + (size_t)c * J.ldo] = p;
+    J.Qh[r + (size_t)c * J.ldo] = q;
+  }
+  __syncthreads();
+  // Alg. 1 on the columns, one warp, compacting kept pairs in place
+  if (tid < 32) {
+    const int lane = tid;
+    int kept = 0;
+    for (int c = 0; c < na; ++c) {
+      double* p = J.Ph + (size_t)c * J.ldo;
+      double* q = J.Qh + (size_t)c * J.ldo;
+      for (int j = 0; j < kept; ++j) {
+        const double* pj = J.Ph + (size_t)j * J.ldo;
+        const double* qj = J.Qh + (size_t)j * J.ldo;
+        double r = 0.0;
+        for (int i = lane; i < d; i += 32) r = fma(qj[i], p[i], r);
+        r = warp_sum(r);
+        for (int i = lane; i < d; i += 32) p[i] = fma(-r, pj[i], p[i]);
+        __syncwarp();
+        double s = 0.0;
+        for (int i = lane; i < d; i += 32) s = fma(pj[i], q[i], s);
+        s = warp_sum(s);
+        for (int i = lane; i < d; i += 32) q[i] = fma(-s, qj[i], q[i]);
+        __syncwarp();
+      }
+      double eta = 0.0;
+      for (int i = lane; i < d; i += 32) eta = fma(p[i], q[i], eta);
+      eta = warp_sum(eta);
+      if (!isfinite(eta) || !(fabs(eta) > J.tau * refp[c] * refq[c])) continue;
+      const double root = sqrt(fabs(eta));
+      const double rr = (eta > 0.0 ? root : -root);
+      double* po = J.Ph + (size_t)kept * J.ldo;
+      double* qo = J.Qh + (size_t)kept * J.ldo;
+      for (int i = lane; i < d; i += 32) {
+        const double pv = p[i] / rr, qv = q[i] / root;
+        po[i] = pv;
+        qo[i] = qv;
+      }
+      __syncwarp();
+      ++kept;
+    }
+    if (lane == 0) *J.count = kept;
+  }
+}
+
+// ------------------------------------------------- Alg. 1, coefficient form
+__global__ void __launch_bounds__(512)
+biorth_coef_kernel(int m, const double* __restrict__ G2, int ld2,
+                   const double* __restrict__ refw2, const double* __restrict__ refz2,
+                   double tau, double* __restrict__ A, double* __restrict__ B, int ldc,
+                   double* __restrict__ work, int* __restrict__ count) {
+  extern __shared__ double sh[];
+  double* a = sh;          // m
+  double* b = a + m;       // m
+  double* u = b + m;       // m
+  __shared__ int s_kept, s_take;
+  double* Uc = work;                 // m x m: u_j = Sxy b_j
+  double* Vc = Uc + (size_t)m * m;   // m x m: v_j = Sxy^T a_j
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+#define SXY(t, s) G2[(t) + (size_t)(m + (s)) * ld2]
+  if (tid == 0) s_kept = 0;
+  __syncthreads();
+  for (int l = 0; l < m; ++l) {
+    const int kept = s_kept;
+    if (tid < 32) {
+      for (int i = lane; i < m; i += 32) { a[i] = (i == l); b[i] = (i == l); }
+      __syncwarp();
+      for (int j = 0; j < kept; ++j) {
+        double r = 0.0;
+        for (int i = lane; i < m; i += 32) r = fma(Uc[i + (size_t)j * m], a[i], r);
+        r = warp_sum(r);
+        for (int i = lane; i < m; i += 32) a[i] = fma(-r, A[i + (size_t)j * ldc], a[i]);
+        double s = 0.0;
+        for (int i = lane; i < m; i += 32) s = fma(Vc[i + (size_t)j * m], b[i], s);
+        s = warp_sum(s);
+        for (int i = lane; i < m; i += 32) b[i] = fma(-s, B[i + (size_t)j * ldc], b[i]);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < m; t += nt) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = fma(SXY(t, k), b[k], s);
+      u[t] = s;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      double eta = 0.0;
+      for (int i = lane; i < m; i += 32) eta = fma(a[i], u[i], eta);
+      eta = warp_sum(eta);
+      const double rw = refw2 ? sqrt(refw2[l]) : sqrt(G2[l + (size_t)l * ld2]);
+      const double rz = refz2 ? sqrt(refz2[l]) : sqrt(G2[(m + l) + (size_t)(m + l) * ld2]);
+      const int take = isfinite(eta) && (fabs(eta) > tau * rw * rz);
+      if (take) {
+        const double root = sqrt(fabs(eta));
+        const double rr = eta > 0.0 ? root : -root;
+        for (int i = lane; i < m; i += 32) {
+          a[i] /= rr;
+          b[i] /= root;
+          u[i] /= root;
+          A[i + (size_t)kept * ldc] = a[i];
+          B[i + (size_t)kept * ldc] = b[i];
+          Uc[i + (size_t)kept * m] = u[i];
+        }
+      }
+      if (lane == 0) s_take = take;
+    }
+    __syncthreads();
+    if (s_take) {
+      for (int s = tid; s < m; s += nt) {
+        double v = 0.0;
+        for (int t = 0; t < m; ++t) v = fma(SXY(t, s), a[t], v);
+        Vc[s + (size_t)kept * m] = v;
+      }
+      __syncthreads();
+      if (tid == 0) s_kept = kept + 1;
+    }
+    __syncthreads();
+  }
+#undef SXY
+  // zero the unused coefficient columns
+  const int kept = s_kept;
+  for (int e = tid; e < m * (m - kept); e += nt) {
+    const int i = e % m, j = kept + e / m;
+    A[i + (size_t)j * ldc] = 0.0;
+    B[i + (size_t)j * ldc] = 0.0;
+  }
+  if (tid == 0) *count = kept;
+}
+
+__global__ void biorth_error_kernel(int d, const double* __restrict__ S, int lds,
+                                    double* __restrict__ out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+    const int i = e % d, j = e / d;
+    m = fmax(m, fabs(S[i + (size_t)j * lds] - (i == j ? 1.0 : 0.0)));
+  }
+  m = block_max(m, red);
+  if (threadIdx.x == 0) *out = m;
+}
+
+// One thread: L L^T = G (r x r), then Cinv = L^-T.
+__global__ void chol_upper_inverse_kernel(int r, const double* __restrict__ G, int ldg,
+                                          double* __restrict__ Cinv, int ldc,
+                                          double* __restrict__ L, int* __restrict__ info) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int j = 0; j < r; ++j)
+    for (int i = 0; i < r; ++i) L[i + j * r] = (i >= j) ? 0.5 * (G[i + j * ldg] + G[j + i * ldg]) : 0.0;
+  for (int j = 0; j < r; ++j) {
+    double v = L[j + j * r];
+    for (int k = 0; k < j; ++k) v -= L[j + k * r] * L[j + k * r];
+    if (!(v > 0.0) || !isfinite(v)) { *info = 1; return; }
+    const double piv = sqrt(v);
+    L[j + j * r] = piv;
+    for (int i = j + 1; i < r; ++i) {
+      double s = L[i + j * r];
+      for (int k = 0; k < j; ++k) s -= L[i + k * r] * L[j + k * r];
+      L[i + j * r] = s / piv;
+    }
+  }
+  // Linv (lower) by forward substitution on unit vectors; Cinv = Linv^T
+  for (int c = 0; c < r; ++c) {
+    for (int i = 0; i < r; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) s -= L[i + k * r] * Cinv[c + k * ldc];
+      Cinv[c + i * ldc] = (i < c) ? 0.0 : s / L[i + i * r];
+    }
+  }
+  *info = 0;
+}
+
+}  // namespace
+
+cudaError_t chol_upper_inverse(int r, const double* G, int ldg, double* Cinv,
+                               int ldc, double* work, int* info, cudaStream_t st) {
+  if (r <= 0) return cudaSuccess;
+  chol_upper_inverse_kernel<<<1, 32, 0, st>>>(r, G, ldg, Cinv, ldc, work, info); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+size_t small_work_elems(int d) { return (size_t)4 * d * d; }
+
+cudaError_t small_lrep_batched(const SmallJob* jobs_dev, int njobs, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  small_lrep_kernel<<<njobs, SMALL_T, 0, st>>>(jobs_dev); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t small_lrep_one(const SmallJob& job, cudaStream_t st) {
+  if (job.d <= 0 || job.d > SMALL_MAXD) return cudaErrorInvalidValue;
+  small_lrep_one_kernel<<<1, SMALL_T, 0, st>>>(job); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+size_t pq_work_elems(int d, int na) { return (size_t)4 * d * (na > 0 ? na : 1); }
+
+cudaError_t small_pq(const PqJob& job, cudaStream_t st) {
+  if (job.na > 64 || job.d > SMALL_MAXD) return cudaErrorInvalidValue;
+  small_pq_kernel<<<1, 256, 0, st>>>(job); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+size_t biorth_coef_work_elems(int m) { return (size_t)2 * m * m; }
+
+cudaError_t biorth_coef(int m, const double* G2, int ld2, const double* ref_w2,
+                        const double* ref_z2, double tau, double* A, double* B,
+                        int ldc, double* work, int* count, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const size_t shm = (size_t)3 * m * sizeof(double);
+  if (shm > 48 * 1024) return cudaErrorInvalidValue;
+  biorth_coef_kernel<<<1, 512, shm, st>>>(m, G2, ld2, ref_w2, ref_z2, tau, A, B,
+                                          ldc, work, count); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t biorth_error(int d, const double* S, int lds, double* out, cudaStream_t st) {
+  biorth_error_kernel<<<1, 512, 0, st>>>(d, S, lds, out); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+}  // namespace lrep

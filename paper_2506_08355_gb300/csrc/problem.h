@@ -1,0 +1,123 @@
+// Problem object behind the C ABI (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lrep.h"
+#include "kernels.h"
+
+namespace lrep {
+
+enum OpKind { OP_DENSE = 0, OP_CSR = 1, OP_STENCIL = 2, OP_CALLBACK = 3 };
+
+// Device arena: one cudaMalloc, bump allocation, zero-filled.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, off = 0;
+  cudaError_t reserve(size_t bytes);
+  template <class T>
+  T* take(size_t count) {
+    const size_t a = 256;
+    off = (off + a - 1) / a * a;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return off <= cap ? p : nullptr;
+  }
+  void release();
+};
+
+struct Operator {
+  int kind = OP_DENSE;
+  int64_t n = 0;
+  // dense (column-major, ld)
+  double* K = nullptr;
+  double* M = nullptr;
+  int64_t ld = 0;
+  // csr
+  int64_t* rpK = nullptr;
+  int32_t* ciK = nullptr;
+  double* vK = nullptr;
+  int64_t* rpM = nullptr;
+  int32_t* ciM = nullptr;
+  double* vM = nullptr;
+  // stencil
+  int nx = 0, ny = 0, nz = 0;
+  double coef_h2 = 0.0;
+  double* dK = nullptr;
+  double* dM = nullptr;
+  // callback
+  lrep_apply_fn fn = nullptr;
+  void* user = nullptr;
+  // mixed precision split (hi/lo bf16) of dense K and M, row-major = col-major
+  void* Khi = nullptr;
+  void* Klo = nullptr;
+  void* Mhi = nullptr;
+  void* Mlo = nullptr;
+  std::vector<void*> owned;  // device allocations freed at destroy
+};
+
+struct lrep_solver;  // forward
+
+}  // namespace lrep
+
+struct lrep_problem_s {
+  lrep::Operator op;
+  cudaStream_t stream = nullptr;
+  lrep_options opts{};
+  std::string err;
+  // nullspace (caller input, device copies)
+  int r = 0;
+  double* X0in = nullptr;
+  double* Y0in = nullptr;
+  // optional start
+  int start_cols = 0;
+  double* U0 = nullptr;
+  double* V0 = nullptr;
+  // results (device, n x nconv, ld = res_ld)
+  int nconv = 0;
+  int nev_solved = 0;
+  std::vector<double> lam;
+  std::vector<double> resid;
+  std::vector<double> history;
+  double* Xres = nullptr;
+  double* Yres = nullptr;
+  int64_t res_ld = 0;
+  int iters = 0;
+  int64_t matvecs = 0;
+  int rebiorths = 0;
+  double timings[5] = {0, 0, 0, 0, 0};
+  double biorth_err = 0.0;
+  bool solved = false;
+  // operator-product profile (options.profile)
+  double prof[4] = {0, 0, 0, 0};
+  // scratch for op-level calls on this problem
+  lrep::Arena op_arena;
+  // solver workspace (kept between solves of the same shape)
+  lrep::Arena ws;
+  size_t ws_key[4] = {0, 0, 0, 0};
+
+  lrep_status fail(lrep_status st, const std::string& msg) {
+    err = msg;
+    return st;
+  }
+};
+
+namespace lrep {
+// y = op(X) with the problem's float64 operator; skip: device flag (CG).
+lrep_status apply_op(lrep_problem p, int which, int c, const double* X,
+                     int64_t ldx, double* Y, int64_t ldy, const int* skip,
+                     double* ws, size_t ws_elems);
+// y = op(X) with the CG (possibly low-precision) operator.
+lrep_status apply_op_cg(lrep_problem p, int which, int c, const double* X,
+                        int64_t ldx, double* Y, int64_t ldy, const int* skip,
+                        double* ws, size_t ws_elems);
+size_t apply_ws_elems(lrep_problem p, int c);
+lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol);
+// mixed precision: build the bf16 hi/lo split of the dense operator
+lrep_status build_split(lrep_problem p);
+void free_split(lrep_problem p);
+}  // namespace lrep

@@ -197,6 +197,31 @@ def serving_trace(num: int = 1000, seed: int = 4, rate_hz: float = 200.0,
 # the configurations the solver is measured on
 
 
+def _cached(name, make):
+    """Generated arrays are cached under $LREP_SYNTH_CACHE (default a
+    per-user directory in the system temp dir) keyed by name."""
+    import os
+    import tempfile
+    base = os.environ.get("LREP_SYNTH_CACHE",
+                          os.path.join(tempfile.gettempdir(), "lrep_synth_cache"))
+    path = os.path.join(base, name + ".npz")
+    if os.path.exists(path):
+        try:
+            with np.load(path) as z:
+                return {k: (z[k] if z[k].ndim else z[k].item()) for k in z.files}
+        except Exception:
+            pass
+    out = make()
+    try:
+        os.makedirs(base, exist_ok=True)
+        tmp = path + ".%d.tmp.npz" % os.getpid()
+        np.savez(tmp, **{k: np.asarray(v) for k, v in out.items()})
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return out
+
+
 def config(idx: int):
     """Problem description of workload ``idx`` (0..3); see module docstring."""
     if idx == 0:
@@ -204,7 +229,8 @@ def config(idx: int):
         p.update(nev=4, block=4, tol=1e-10, name="dense-fp64-n200")
         return p
     if idx == 1:
-        p = haar_dense(8192, seed=1, n_zero_k=4)
+        p = _cached("haar_dense_8192_seed1_null4",
+                    lambda: haar_dense(8192, seed=1, n_zero_k=4))
         p.update(nev=64, block=16, tol=1e-10, name="dense-fp64-n8192-null4")
         return p
     if idx == 2:

@@ -1,0 +1,195 @@
+"""Per-step parity of the CUDA kernels with the FP64 oracle, through the
+C ABI (include/lrep_ops.h).  Sizes span several tiles and a ragged tail.
+
+Tolerances for float64 products follow the standard rounding bound: two
+evaluations of a length-k dot product in different orders differ by at
+most 2 * gamma_k * (|a|^T |b|), gamma_k = k u / (1 - k u), u = 2^-53.
+"""
+import numpy as np
+import pytest
+
+from conftest import from_dev, to_dev
+from oracle import lrep_ref as R
+from oracle.philox import normal_block
+from paper_2506_08355_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+def bound(A, B, k):
+    g = k * U / (1 - k * U)
+    return 2.0 * g * (np.abs(A) @ np.abs(B)) + 1e-300
+
+
+@pytest.fixture(scope="module")
+def L(built_lib):
+    from paper_2506_08355_gb300 import lrep
+    return lrep
+
+
+def test_dense_apply_ragged(L):
+    rng = np.random.default_rng(0)
+    n, c = 1000, 37
+    A = rng.standard_normal((n, n))
+    K = A + A.T
+    M = K @ K / n + np.eye(n)
+    X = rng.standard_normal((n, c))
+    p = L.Problem.dense(K, M)
+    Xd = to_dev(X)
+    Y = L.device_block(n, c)
+    for op, mat in ((L.OP_K, K), (L.OP_M, M)):
+        p.apply(op, Xd, Y)
+        got = from_dev(Y)
+        ref = R.DenseOp(K, M).apply("K" if op == L.OP_K else "M", X)
+        assert np.all(np.abs(got - ref) <= bound(mat, X, n))
+    p.close()
+
+
+def test_dense_apply_split_k_sampled(L):
+    """n = 8192, 16 columns (the CG product of the 8192 workload), split-K."""
+    rng = np.random.default_rng(1)
+    n, c = 8192, 16
+    A = rng.standard_normal((n, n))
+    K = (A + A.T) * 0.5
+    X = rng.standard_normal((n, c))
+    p = L.Problem.dense(K, K)
+    Y = L.device_block(n, c)
+    p.apply(L.OP_K, to_dev(X), Y)
+    got = from_dev(Y)
+    rows = rng.choice(n, 64, replace=False)
+    ref = K[rows] @ X
+    assert np.all(np.abs(got[rows] - ref) <= bound(K[rows], X, n))
+    p.close()
+
+
+def test_stencil_and_csr_apply(L):
+    nx, ny, nz = 20, 17, 13
+    s = synth.bdg_stencil(nx, ny, nz)
+    op = R.StencilOp(nx, ny, nz, s["h"], -0.5, s["dK"], s["dM"])
+    n = op.n
+    X = np.random.default_rng(2).standard_normal((n, 19))
+    ps = L.Problem.stencil(nx, ny, nz, s["h"], -0.5, s["dK"], s["dM"])
+    csrK = synth.stencil_to_csr(nx, ny, nz, s["h"], -0.5, s["dK"])
+    csrM = synth.stencil_to_csr(nx, ny, nz, s["h"], -0.5, s["dM"])
+    pc = L.Problem.csr(n, csrK, csrM)
+    Y = L.device_block(n, 19)
+    for op_id, w in ((L.OP_K, "K"), (L.OP_M, "M")):
+        ref = op.apply(w, X)
+        scale = np.abs(op.c) * 7 * np.abs(X).max() + np.abs(op.dK).max() * np.abs(X).max()
+        for prob in (ps, pc):
+            prob.apply(op_id, to_dev(X), Y)
+            np.testing.assert_allclose(from_dev(Y), ref, rtol=0, atol=1e-14 * scale)
+    ps.close()
+    pc.close()
+
+
+@pytest.mark.parametrize("n,a,b", [(5000, 45, 70), (33, 3, 1), (70000, 16, 16), (4097, 80, 80)])
+def test_gram(L, n, a, b):
+    import torch
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, a))
+    B = rng.standard_normal((n, b))
+    G = torch.zeros((b, a), dtype=torch.float64, device="cuda")
+    L.gram(to_dev(A), to_dev(B), G)
+    torch.cuda.synchronize()
+    got = G.cpu().numpy().T
+    assert np.all(np.abs(got - A.T @ B) <= bound(A.T, B, n))
+
+
+def test_update(L):
+    import torch
+    rng = np.random.default_rng(3)
+    n, k, c = 3001, 45, 41
+    A = rng.standard_normal((n, k))
+    Bm = rng.standard_normal((k, c))
+    C0 = rng.standard_normal((n, c))
+    Cd = to_dev(C0)
+    L.update(to_dev(A), to_dev(Bm), Cd, 0.5, -2.0)
+    torch.cuda.synchronize()
+    ref = 0.5 * C0 - 2.0 * (A @ Bm)
+    tolm = 2.0 * bound(A, Bm, k + 1) + 4 * U * np.abs(C0)
+    assert np.all(np.abs(from_dev(Cd) - ref) <= tolm)
+
+
+@pytest.mark.parametrize("d", [1, 12, 37, 80, 160])
+def test_small_lrep(L, d):
+    import torch
+    rng = np.random.default_rng(d)
+    A = rng.standard_normal((d, d))
+    Bq = rng.standard_normal((d, d))
+    Kh = A @ A.T + 0.5 * np.eye(d)
+    Mh = Bq @ Bq.T + 0.5 * np.eye(d)
+    lam_r, Xr, Yr = R.small_lrep(Kh, Mh)
+    lam = torch.zeros(d, dtype=torch.float64, device="cuda")
+    Xh = torch.zeros((d, d), dtype=torch.float64, device="cuda")
+    Yh = torch.zeros((d, d), dtype=torch.float64, device="cuda")
+    info = L.small_lrep(to_dev(Kh), to_dev(Mh), lam, Xh, Yh)
+    assert info == 0
+    lg, Xg, Yg = lam.cpu().numpy(), from_dev(Xh), from_dev(Yh)
+    np.testing.assert_allclose(lg, lam_r, rtol=1e-11)
+    # unique up to the sign of each pair (simple spectrum)
+    sg = np.sign(np.sum(Xg * Xr, axis=0))
+    np.testing.assert_allclose(Xg * sg, Xr, atol=1e-9 * np.abs(Xr).max())
+    np.testing.assert_allclose(Yg * sg, Yr, atol=1e-9 * np.abs(Yr).max())
+    np.testing.assert_allclose(Xg.T @ Yg, np.eye(d), atol=1e-11)
+
+
+def test_small_lrep_not_spd(L):
+    import torch
+    d = 6
+    Kh = np.diag([1.0, 2.0, -1.0, 3.0, 4.0, 5.0])
+    lam = torch.zeros(d, dtype=torch.float64, device="cuda")
+    Xh = torch.zeros((d, d), dtype=torch.float64, device="cuda")
+    Yh = torch.zeros((d, d), dtype=torch.float64, device="cuda")
+    assert L.small_lrep(to_dev(Kh), to_dev(np.eye(d)), lam, Xh, Yh) == 1
+    assert L.small_lrep(to_dev(np.eye(d)), to_dev(Kh), lam, Xh, Yh) == 2
+
+
+def test_biorth_matches_alg1(L):
+    """The biorthogonal pair is unique (LU of W^T Z with the Alg. 1
+    normalisation), so GPU and the literal Alg. 1 agree column by column,
+    including which pair is discarded."""
+    rng = np.random.default_rng(5)
+    n, m = 3000, 24
+    W = rng.standard_normal((n, m))
+    Z = W + 0.5 * rng.standard_normal((n, m))
+    W[:, 7] = W[:, 2] - 0.5 * W[:, 5]
+    Z[:, 7] = Z[:, 2] - 0.5 * Z[:, 5]   # pair 7 in the span of pairs 2, 5
+    Pr, Qr, kept = R.mgs_biorth(W, Z)
+    P = L.device_block(n, m)
+    Q = L.device_block(n, m)
+    k = L.biorth(to_dev(W), to_dev(Z), P, Q)
+    assert k == len(kept) == m - 1
+    Pg, Qg = from_dev(P)[:, :k], from_dev(Q)[:, :k]
+    np.testing.assert_allclose(Pg, Pr, atol=1e-9 * np.abs(Pr).max())
+    np.testing.assert_allclose(Qg, Qr, atol=1e-9 * np.abs(Qr).max())
+    np.testing.assert_allclose(Pg.T @ Qg, np.eye(k), atol=1e-12)
+
+
+def test_residuals(L):
+    import torch
+    rng = np.random.default_rng(6)
+    n, w = 2500, 9
+    X, Y = rng.standard_normal((n, w)), rng.standard_normal((n, w))
+    KX, MY = rng.standard_normal((n, w)), rng.standard_normal((n, w))
+    lam = rng.uniform(0.1, 2.0, w)
+    eps = torch.zeros(w, dtype=torch.float64, device="cuda")
+    L.residuals(to_dev(X), to_dev(Y), to_dev(KX), to_dev(MY),
+                torch.from_numpy(lam).cuda(), eps)
+
+    class Fixed:
+        def apply(self, which, Z):
+            return KX if which == "K" else MY
+    ref = R.residuals(Fixed(), X, Y, lam)
+    np.testing.assert_allclose(eps.cpu().numpy(), ref, rtol=1e-13)
+
+
+def test_philox_normals(L):
+    import torch
+    n, c = 1001, 7
+    out = L.device_block(n, c)
+    L.philox_normal(n, c, 0x123456789ABCDEF, 1, out)
+    torch.cuda.synchronize()
+    ref = normal_block(n, c, 0x123456789ABCDEF, 1)
+    np.testing.assert_allclose(from_dev(out), ref, rtol=1e-13, atol=1e-14)

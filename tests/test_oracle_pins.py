@@ -116,6 +116,14 @@ def test_definition_bruteforce_eig_of_H_and_pairing():
     np.testing.assert_allclose(H @ xi, -lam[0] * xi, atol=1e-12)
 
 
+def test_definition_values_only_route():
+    p = synth.haar_dense(50, seed=9, n_zero_k=2)
+    lam, X, Y = R.lrep_definition(p["K"], p["M"], 10, r=2)
+    FK = p["Q1"] * np.sqrt(p["k"])[None, :]
+    FM = p["Q2"] * np.sqrt(p["m"])[None, :]
+    np.testing.assert_allclose(R.lrep_definition_values(FK, FM, 10, r=2), lam, rtol=1e-12)
+
+
 def test_trace_minimisation_principle():
     """Thm. minimization principles: sum of the k smallest lam equals
     1/2 tr(U^T K U + V^T M V) at the eigenvectors and is a lower bound for
