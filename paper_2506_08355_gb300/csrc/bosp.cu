@@ -42,8 +42,9 @@ void Arena::release() {
 }
 
 size_t apply_ws_elems(lrep_problem p, int c) {
-  if (p->op.kind == OP_DENSE) return dense_apply_ws_elems(p->op.n, c);
-  return 0;
+  size_t w = 0;
+  if (p->op.kind == OP_DENSE) w = dense_apply_ws_elems(p->op.n, c);
+  return std::max(w, apply_cg_ws_elems(p, c));
 }
 
 lrep_status apply_op(lrep_problem p, int which, int c, const double* X,
@@ -140,6 +141,7 @@ struct Solver {
     int info;
     int cnt[4];
     int cg_iters;
+    int tc_err;
     int act[64];
     double lam_act[64];
   }* h = nullptr;
@@ -495,8 +497,14 @@ struct Solver {
     LCK(cudaMemcpyAsync(h->eps, eps_d, sizeof(double) * e, cudaMemcpyDeviceToHost, st));
     LCK(cudaMemcpyAsync(&h->berr, berr_d, sizeof(double), cudaMemcpyDeviceToHost, st));
     LCK(cudaMemcpyAsync(&h->info, info_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    h->tc_err = 0;
+    if (p->op.tc_err)
+      LCK(cudaMemcpyAsync(&h->tc_err, p->op.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     if (events) LCK(cudaEventRecord(ev[2], st));
     LST(sync());
+    if (h->tc_err)
+      return p->fail(LREP_ERR_CUDA, "tensor-core pipeline wait expired (code " +
+                                        std::to_string(h->tc_err) + ")");
     if (h->info == 1 || h->info == 2)
       return p->fail(LREP_ERR_NOT_SPD,
                      h->info == 1 ? "projected K^ = U^T K U is not positive definite "

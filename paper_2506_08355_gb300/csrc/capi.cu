@@ -431,8 +431,15 @@ lrep_status lrep_op_apply_cg(lrep_problem p, int32_t op, int32_t ncols, const do
   const size_t ws = apply_ws_elems(p, ncols);
   if (p->op_arena.cap < (ws + 64) * sizeof(double))
     PCK(p, p->op_arena.reserve((ws + 64) * sizeof(double)));
-  return apply_op_cg(p, op, ncols, X, ldx, Y, ldy, nullptr,
-                     reinterpret_cast<double*>(p->op_arena.base), ws);
+  lrep_status s = apply_op_cg(p, op, ncols, X, ldx, Y, ldy, nullptr,
+                              reinterpret_cast<double*>(p->op_arena.base), ws);
+  if (s == LREP_OK && p->op.tc_err) {
+    int h = 0;
+    PCK(p, cudaMemcpyAsync(&h, p->op.tc_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    PCK(p, cudaStreamSynchronize(p->stream));
+    if (h) return p->fail(LREP_ERR_CUDA, "tensor-core pipeline wait expired");
+  }
+  return s;
 }
 
 lrep_status lrep_op_gram(int64_t n, int32_t a, int32_t b, const double* A, int64_t lda,

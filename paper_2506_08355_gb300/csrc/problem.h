@@ -11,6 +11,7 @@
 #include "kernels.h"
 
 namespace lrep {
+struct TcOperand;
 
 enum OpKind { OP_DENSE = 0, OP_CSR = 1, OP_STENCIL = 2, OP_CALLBACK = 3 };
 
@@ -52,11 +53,10 @@ struct Operator {
   // callback
   lrep_apply_fn fn = nullptr;
   void* user = nullptr;
-  // mixed precision split (hi/lo bf16) of dense K and M, row-major = col-major
-  void* Khi = nullptr;
-  void* Klo = nullptr;
-  void* Mhi = nullptr;
-  void* Mlo = nullptr;
+  // mixed precision: bf16 hi/lo split of dense K and M (tc.h)
+  struct TcOperand* tcK = nullptr;
+  struct TcOperand* tcM = nullptr;
+  int* tc_err = nullptr;  // pipeline timeout flag of the tensor-core kernel
   std::vector<void*> owned;  // device allocations freed at destroy
 };
 
@@ -116,6 +116,7 @@ lrep_status apply_op_cg(lrep_problem p, int which, int c, const double* X,
                         int64_t ldx, double* Y, int64_t ldy, const int* skip,
                         double* ws, size_t ws_elems);
 size_t apply_ws_elems(lrep_problem p, int c);
+size_t apply_cg_ws_elems(lrep_problem p, int c);
 lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol);
 // mixed precision: build the bf16 hi/lo split of the dense operator
 lrep_status build_split(lrep_problem p);

@@ -335,7 +335,7 @@ class Problem:
     def apply(self, op, X, Y, cg=False):
         """Y = op(X) for device blocks X, Y (torch (c, ld))."""
         f = lib().lrep_op_apply_cg if cg else lib().lrep_op_apply
-        _check(f(self.h, op, X.shape[0], _ptr(X), X.stride(0), _ptr(Y), Y.stride(0)), self.h)
+        _check(f(self.h, op, X.shape[0], _ptr(X), _ld(X), _ptr(Y), _ld(Y)), self.h)
 
     def close(self):
         if self.h:
@@ -352,6 +352,12 @@ class Problem:
 # ------------------------------------------------------------- op level
 
 
+def _ld(t):
+    """Leading dimension of a (c, ld) device block (size-1 dims carry no
+    meaningful stride)."""
+    return t.stride(0) if t.shape[0] > 1 else t.shape[1]
+
+
 def _st(stream):
     if stream is None:
         import torch
@@ -362,23 +368,23 @@ def _st(stream):
 def gram(A, B, G, stream=None):
     """G (b, a) tensor <- A^T B for device blocks A (a, n), B (b, n)."""
     n = A.shape[1]
-    _check(lib().lrep_op_gram(n, A.shape[0], B.shape[0], _ptr(A), A.stride(0), _ptr(B),
-                              B.stride(0), _ptr(G), G.stride(0), _st(stream)))
+    _check(lib().lrep_op_gram(n, A.shape[0], B.shape[0], _ptr(A), _ld(A), _ptr(B),
+                              _ld(B), _ptr(G), _ld(G), _st(stream)))
 
 
 def update(A, B, Cm, alpha, beta, stream=None):
     """Cm <- alpha Cm + beta A B for device A (k, n), B (c, k), Cm (c, n)."""
     n = A.shape[1]
-    _check(lib().lrep_op_update(n, A.shape[0], Cm.shape[0], alpha, _ptr(A), A.stride(0),
-                                _ptr(B), B.stride(0), beta, _ptr(Cm), Cm.stride(0),
+    _check(lib().lrep_op_update(n, A.shape[0], Cm.shape[0], alpha, _ptr(A), _ld(A),
+                                _ptr(B), _ld(B), beta, _ptr(Cm), _ld(Cm),
                                 _st(stream)))
 
 
 def small_lrep(Kh, Mh, lam, Xh, Yh, stream=None):
     d = Kh.shape[0]
     info = C.c_int32()
-    _check(lib().lrep_op_small_lrep(d, _ptr(Kh), _ptr(Mh), Kh.stride(0), _ptr(lam),
-                                    _ptr(Xh), _ptr(Yh), Xh.stride(0), C.byref(info),
+    _check(lib().lrep_op_small_lrep(d, _ptr(Kh), _ptr(Mh), _ld(Kh), _ptr(lam),
+                                    _ptr(Xh), _ptr(Yh), _ld(Xh), C.byref(info),
                                     _st(stream)))
     return info.value
 
@@ -386,15 +392,15 @@ def small_lrep(Kh, Mh, lam, Xh, Yh, stream=None):
 def biorth(W, Z, P, Q, tau=1e-10, stream=None):
     n = W.shape[1]
     kept = C.c_int32()
-    _check(lib().lrep_op_biorth(n, W.shape[0], _ptr(W), _ptr(Z), W.stride(0), tau,
-                                _ptr(P), _ptr(Q), P.stride(0), C.byref(kept), _st(stream)))
+    _check(lib().lrep_op_biorth(n, W.shape[0], _ptr(W), _ptr(Z), _ld(W), tau,
+                                _ptr(P), _ptr(Q), _ld(P), C.byref(kept), _st(stream)))
     return kept.value
 
 
 def residuals(X, Y, KX, MY, lam, eps, stream=None):
     n = X.shape[1]
     _check(lib().lrep_op_residuals(n, X.shape[0], _ptr(X), _ptr(Y), _ptr(KX), _ptr(MY),
-                                   X.stride(0), _ptr(lam), _ptr(eps), _st(stream)))
+                                   _ld(X), _ptr(lam), _ptr(eps), _st(stream)))
 
 
 def launch_count():
@@ -403,7 +409,7 @@ def launch_count():
 
 
 def philox_normal(n, ncols, seed, stream_id, out, stream=None):
-    _check(lib().lrep_op_philox_normal(n, ncols, seed, stream_id, _ptr(out), out.stride(0),
+    _check(lib().lrep_op_philox_normal(n, ncols, seed, stream_id, _ptr(out), _ld(out),
                                        _st(stream)))
 
 

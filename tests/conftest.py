@@ -36,7 +36,7 @@ def to_dev(a):
     a = np.asarray(a, dtype=np.float64)
     if a.ndim == 1:
         a = a[:, None]
-    return torch.from_numpy(np.ascontiguousarray(a.T)).cuda()
+    return torch.tensor(np.ascontiguousarray(a.T), dtype=torch.float64, device="cuda").contiguous()
 
 
 def from_dev(t):

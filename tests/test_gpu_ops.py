@@ -193,3 +193,29 @@ def test_philox_normals(L):
     torch.cuda.synchronize()
     ref = normal_block(n, c, 0x123456789ABCDEF, 1)
     np.testing.assert_allclose(from_dev(out), ref, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("n,c", [(1000, 16), (1000, 1), (777, 37), (4096, 32)])
+def test_bf16x3_tensor_core_product(L, n, c):
+    """Mixed-precision CG product (tcgen05, bf16 hi/lo split, fp32
+    accumulation) against the float64 product.  Error model: dropping the
+    lo*lo term and rounding lo leave ~2^-16 relative per operand, fp32
+    accumulation adds ~k 2^-24; bound 1e-4 of |A||X| with margin."""
+    rng = np.random.default_rng(n + c)
+    A = rng.standard_normal((n, n))
+    K = (A + A.T) * 0.5
+    M = K @ K / n + np.eye(n)
+    X = rng.standard_normal((n, c))
+    p = L.Problem.dense(K, M)
+    p.set_options(precision=L.PREC_MIXED_BF16X3)
+    Y = L.device_block(n, c)
+    for op, mat in ((L.OP_K, K), (L.OP_M, M)):
+        p.apply(op, to_dev(X), Y, cg=True)
+        got = from_dev(Y)
+        ref = mat @ X
+        scale = np.abs(mat) @ np.abs(X)
+        err = np.abs(got - ref) / scale
+        assert err.max() < 1e-4, err.max()
+        # and it is not the float64 path: the error is visibly non-zero
+        assert err.max() > 1e-12
+    p.close()

@@ -204,3 +204,23 @@ def test_invalid_options_rejected(L):
     with pytest.raises(L.LrepError):
         prob.nconv()  # query before solve
     prob.close()
+
+
+def test_mixed_precision_config0_and_moving(L):
+    """Mixed mode: tensor-core CG products, float64 Rayleigh-Ritz and
+    residuals; same eigenvalues as the FP64 oracle (1e-10 relative)."""
+    p = synth.config(0)
+    lam_r, _, _ = R.lrep_definition(p["K"], p["M"], 4)
+    prob = L.Problem.dense(p["K"], p["M"])
+    prob.set_options(precision=L.PREC_MIXED_BF16X3)
+    assert prob.solve(4, 4, 1e-10) == L.OK
+    check(R.DenseOp(p["K"], p["M"]), prob, lam_r, 1e-10, 4)
+    prob.close()
+    q = synth.haar_dense(1000, seed=1, n_zero_k=4)
+    lam_r, _, _ = R.lrep_definition(q["K"], q["M"], 64, r=4)
+    prob = L.Problem.dense(q["K"], q["M"])
+    prob.set_nullspace(q["X0"])
+    prob.set_options(precision=L.PREC_MIXED_BF16X3)
+    assert prob.solve(64, 16, 1e-10) == L.OK
+    check(R.DenseOp(q["K"], q["M"]), prob, lam_r, 1e-10, 64)
+    prob.close()
