@@ -46,6 +46,16 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--op", default=None, choices=["dense", "tc", "small", "stencil", "gram"],
+                    help="time one hot-path step alone (for ncu captures) instead of solves")
+    ap.add_argument("--n", type=int, default=8192, help="order for --op")
+    ap.add_argument("--cols", type=int, default=16, help="block columns for --op")
+    ap.add_argument("--reps", type=int, default=3, help="launches for --op")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving workload: Poisson arrivals through lrep_server_*")
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--pool", type=int, default=48, help="distinct generated problems")
+    ap.add_argument("--slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -54,6 +64,17 @@ def dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def aggregate(ms, nev, steps, world, td=None, device=None):
+    """Whole-job throughput of `world` replicas: the slowest rank's time
+    (max over ranks) and all ranks' eigenpairs.  Returns (ms_max, value)."""
+    if td is not None and world > 1:
+        import torch
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * nev * steps / (ms / 1000.0)
 
 
 def measured_peaks():
@@ -178,12 +199,199 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- single-step mode
+
+
+def op_mode(args):
+    """One hot-path step repeated --reps times through the C ABI, timed
+    with CUDA events; prints one JSON line (used for kernel captures)."""
+    import torch
+    from paper_2506_08355_gb300 import build, lrep
+    build.build()
+    n, c = args.n, args.cols
+    g = torch.Generator(device="cuda").manual_seed(0)
+    times = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    if args.op in ("dense", "tc"):
+        A = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
+        K = (A + A.T) * 0.5
+        del A
+        p = lrep.Problem.dense(K, K, borrow=True)
+        if args.op == "tc":
+            p.set_options(precision=lrep.PREC_MIXED_BF16X3)
+        X = torch.randn(c, n, dtype=torch.float64, device="cuda", generator=g)
+        Y = torch.empty(c, n, dtype=torch.float64, device="cuda")
+        for _ in range(args.reps):
+            ev[0].record()
+            p.apply(lrep.OP_K, X, Y, cg=(args.op == "tc"))
+            ev[1].record()
+            torch.cuda.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]))
+        ref = (K @ X.T).T
+        err = ((Y - ref).abs().max() / (K.abs() @ X.abs().T).max()).item()
+        assert err < (1e-4 if args.op == "tc" else 1e-13), err
+        work = {"flops": 2.0 * n * n * c * (3 if args.op == "tc" else 1),
+                "bytes": (4.0 if args.op == "tc" else 8.0) * n * n + 16.0 * n * c,
+                "max_rel_err": err}
+        p.close()
+    elif args.op == "stencil":
+        from paper_2506_08355_gb300 import synth
+        s = synth.bdg_stencil(args.n)
+        nn = s["n"]
+        p = lrep.Problem.stencil(s["nx"], s["ny"], s["nz"], s["h"], -0.5, s["dK"], s["dM"])
+        X = torch.randn(c, nn, dtype=torch.float64, device="cuda", generator=g)
+        Y = torch.empty(c, nn, dtype=torch.float64, device="cuda")
+        for _ in range(args.reps):
+            ev[0].record()
+            p.apply(lrep.OP_K, X, Y)
+            ev[1].record()
+            torch.cuda.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]))
+        work = {"flops": 9.0 * nn * c, "bytes": (16.0 * c + 8.0) * nn}
+        p.close()
+    elif args.op == "small":
+        d = c
+        A = torch.randn(d, d, dtype=torch.float64, device="cuda", generator=g)
+        B = torch.randn(d, d, dtype=torch.float64, device="cuda", generator=g)
+        Kh = A @ A.T + 0.5 * torch.eye(d, dtype=torch.float64, device="cuda")
+        Mh = B @ B.T + 0.5 * torch.eye(d, dtype=torch.float64, device="cuda")
+        lam = torch.empty(d, dtype=torch.float64, device="cuda")
+        Xh = torch.empty(d, d, dtype=torch.float64, device="cuda")
+        Yh = torch.empty(d, d, dtype=torch.float64, device="cuda")
+        for _ in range(args.reps):
+            ev[0].record()
+            info = lrep.small_lrep(Kh, Mh, lam, Xh, Yh)
+            ev[1].record()
+            torch.cuda.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]))
+            assert info == 0, info
+        work = {"flops": 25.0 * d ** 3, "bytes": 2.0 * 8 * d * d}
+    else:  # gram
+        A = torch.randn(c, n, dtype=torch.float64, device="cuda", generator=g)
+        G = torch.empty(c, c, dtype=torch.float64, device="cuda")
+        for _ in range(args.reps):
+            ev[0].record()
+            lrep.gram(A, A, G)
+            ev[1].record()
+            torch.cuda.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]))
+        work = {"flops": 2.0 * n * c * c, "bytes": 16.0 * n * c}
+    best = min(times)
+    work.update({"op": args.op, "n": n, "cols": c, "reps": args.reps, "ms": times,
+                 "best_ms": best, "gflops": work["flops"] / best / 1e6,
+                 "gbs": work["bytes"] / best / 1e6})
+    print(json.dumps(work), flush=True)
+
+
+# ------------------------------------------------------------- serving
+
+
+def haar_pool(count, seed, device):
+    """`count` dense problems built as the n = 200 workload (Haar Q1, Q2,
+    k, m ~ U[0.5, 10]) with n log-uniform in [256, 4096], generated on the
+    device (input preparation, torch.linalg.qr)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(np.log(256), np.log(4096), size=count))).astype(int)
+    g = torch.Generator(device=device).manual_seed(seed)
+    pool = []
+    for n in sizes:
+        mats = []
+        for _ in range(2):
+            G = torch.randn(n, n, dtype=torch.float64, device=device, generator=g)
+            Q, Rm = torch.linalg.qr(G)
+            Q = Q * torch.sign(torch.diagonal(Rm))[None, :]
+            ev = 0.5 + 9.5 * torch.rand(n, dtype=torch.float64, device=device, generator=g)
+            A = (Q * ev[None, :]) @ Q.T
+            mats.append(0.5 * (A + A.T))
+            del G, Q, Rm
+        pool.append((int(n), mats[0].contiguous(), mats[1].contiguous()))
+    torch.cuda.synchronize()
+    return pool
+
+
+def serve_mode(args):
+    import torch
+    from paper_2506_08355_gb300 import build, lrep, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    t_gen = time.perf_counter()
+    pool = haar_pool(args.pool, 4, dev)
+    t_gen = time.perf_counter() - t_gen
+    trace = synth.serving_trace(num=args.requests, seed=4)
+    # requests use the pool problem closest in size (log scale) to the drawn n
+    logs = np.log([p[0] for p in pool])
+    probs = []
+    for r in trace:
+        k = int(np.argmin(np.abs(logs - np.log(r["n"]))))
+        n, K, M = pool[k]
+        pr = lrep.Problem.dense(K, M, borrow=True)
+        pr.set_options(precision=lrep.PREC_MIXED_BF16X3, seed=r["seed"])
+        probs.append((pr, r["nev"], n, r["t"]))
+    tol = 1e-8
+    srv = lrep.Server(hbm_budget_bytes=200 << 30, max_slots=args.slots)
+    import threading
+    done_at = {}
+    t0 = time.perf_counter()
+    tickets = []
+
+    def submitter():
+        for i, (pr, nev, n, ta) in enumerate(probs):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append((i, srv.submit(pr, nev, nev, tol), time.perf_counter() - t0))
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    status = {}
+    while len(status) < len(probs):
+        for (i, t, ts) in list(tickets):
+            if i in status:
+                continue
+            st = srv.wait(t, 0)
+            if st != -6:
+                status[i] = st
+                done_at[i] = time.perf_counter() - t0
+        time.sleep(0.0005)
+    th.join()
+    makespan = time.perf_counter() - t0
+    sub = {i: ts for (i, t, ts) in tickets}
+    lat = np.array([done_at[i] - sub[i] for i in range(len(probs))]) * 1e3
+    ok = sum(1 for v in status.values() if v == 0)
+    total_nev = sum(p[1] for p in probs)
+    worst = 0.0
+    for pr, nev, n, ta in probs[:: max(1, len(probs) // 50)]:
+        worst = max(worst, float(pr.residuals().max()))
+    stats = srv.stats()
+    srv.close()
+    for pr, *_ in probs:
+        pr.close()
+    line = {"metric": "serving: eigenpairs/s and latency at residual<=1e-8 (mixed path)",
+            "value": total_nev / makespan, "unit": "eigenpairs/s", "n_gpus": 1,
+            "higher_is_better": True, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "requests": len(probs), "ok": ok, "makespan_s": makespan,
+            "sampled_max_residual": worst, "slots": args.slots,
+            "shared_small_lrep_launches": {"batches": stats[0], "problems": stats[1],
+                                           "largest": stats[2]},
+            "dtype": "bf16x3+f64", "data": "synthetic",
+            "config": {"workload": "serving-poisson200-dense-n256-4096-nev4-32-tol1e-8",
+                       "pool": args.pool, "pool_generation_s": t_gen,
+                       "arrivals": "Poisson, mean 200/s (seed 4)"}}
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- ours
 
 
 def main():
     args = parse()
     rank, world, local = dist()
+    if args.op:
+        return op_mode(args)
+    if args.serve:
+        return serve_mode(args)
     if args.impl == "reference":
         return reference_arm(args, rank, world)
     import torch
@@ -227,14 +435,10 @@ def main():
     torch.cuda.synchronize()
     launches = lrep.launch_count() - l0
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms, value = aggregate(ev0.elapsed_time(ev1), nev, args.steps, world, pg, dev)
     if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
         pg.barrier()
     ms_step = ms / args.steps
-    value = world * nev * args.steps / (ms / 1000.0)
     res = prob.residuals()
     assert prob.nconv() == nev and res.max() < tol, (prob.nconv(), res.max())
     # roofline of the dominant kernel: one more profiled solve (per-launch

@@ -189,6 +189,11 @@ lrep_status lrep_destroy(lrep_problem p);
  * order while their HBM footprint fits hbm_budget_bytes and a slot is
  * free.  The problems passed to submit must stay alive until wait returns.
  */
+/* Device bytes a solve of (nev, block) on p needs beyond the operator
+ * itself (solver workspace, plus the bf16 operator split in mixed mode when
+ * it is not built yet): the footprint the server admits requests by. */
+lrep_status lrep_footprint(lrep_problem p, int32_t nev, int32_t block, int64_t* bytes);
+
 lrep_status lrep_server_create(lrep_server* out, int64_t hbm_budget_bytes,
                                int32_t max_slots, void* stream);
 lrep_status lrep_server_submit(lrep_server s, lrep_problem p, int32_t nev,
@@ -196,7 +201,11 @@ lrep_status lrep_server_submit(lrep_server s, lrep_problem p, int32_t nev,
 /* Wait for a ticket with a host-side deadline (timeout_ms < 0: forever).
  * Returns the solve's status, or LREP_ERR_TIMEOUT. */
 lrep_status lrep_server_wait(lrep_server s, uint64_t ticket, int32_t timeout_ms);
+/* Stops accepting work after the queued requests finish, then frees. */
 lrep_status lrep_server_destroy(lrep_server s);
+/* Shared-launch statistics: out3[0] batched small-LREP launches,
+ * out3[1] small problems solved by them, out3[2] largest batch. */
+lrep_status lrep_server_stats(lrep_server s, int64_t* out3);
 
 #ifdef __cplusplus
 }

@@ -151,6 +151,7 @@ struct Solver {
   std::vector<double> locked;
   cudaEvent_t ev[6];
   bool events = false;
+  SmallBatcher* batcher = nullptr;
   struct Pending {
     cudaEvent_t a, b;
     int c;
@@ -484,7 +485,10 @@ struct Solver {
     job.lam = lam_d; job.Xh = Xh; job.Yh = Yh; job.ldo = dmax;
     job.work = swork; job.info = info_d; job.biorth_err = berr_d;
     job.d = d; job.w_prev = w_prev;
-    LCK(small_lrep_one(job, st));
+    if (batcher)
+      LCK(batcher->run(job, st));
+    else
+      LCK(small_lrep_one(job, st));
     const int t = nx();
     LST(update(e, 0.0, sU, Xh, dmax, 1.0, UX[t]));
     LST(update(e, 0.0, sV, Yh, dmax, 1.0, UY[t]));
@@ -754,8 +758,7 @@ struct Solver {
 
 }  // namespace
 
-lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol) {
-  Solver S{};
+static void configure(Solver& S, lrep_problem p, int nev, int nb, double tol) {
   S.p = p;
   S.st = p->stream;
   S.n = p->op.n;
@@ -768,6 +771,35 @@ lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol) {
   S.C = S.w + 4 * S.nb;
   S.Lmax = S.r + nev + S.dmax;
   S.tol = tol;
+}
+
+size_t bosp_footprint(lrep_problem p, int nev, int nb) {
+  Solver S{};
+  configure(S, p, nev, nb, 1.0);
+  S.ld = ((S.n + 31) / 32) * 32;
+  S.cgcols = std::max(S.nb, std::max(S.r, 1));
+  const int dd = 2 * S.dmax, rr = std::max(S.r, 1);
+  size_t wsz = 0;
+  wsz = std::max(wsz, gram_ws_elems(S.n, S.dmax, S.dmax));
+  wsz = std::max(wsz, gram_ws_elems(S.n, dd, dd));
+  wsz = std::max(wsz, gram_ws_elems(S.n, S.Lmax, S.cgcols));
+  wsz = std::max(wsz, gram_ws_elems(S.n, rr, std::max(rr, S.dmax)));
+  wsz = std::max(wsz, gram_ws_elems(S.n, nev, nev));
+  wsz = std::max(wsz, apply_ws_elems(p, std::max(S.C, S.cgcols)));
+  S.ws_elems = wsz;
+  S.part_elems = std::max(residual_ws_elems(S.n, std::max(S.C, nev)),
+                          std::max(colnorm_ws_elems(S.n, S.cgcols), cg_part_elems(S.n, S.cgcols)));
+  Arena dry;
+  dry.base = nullptr;
+  dry.cap = ~(size_t)0;
+  S.layout(dry);
+  return dry.off + 4096;
+}
+
+lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol, SmallBatcher* batcher) {
+  Solver S{};
+  configure(S, p, nev, nb, tol);
+  S.batcher = batcher;
   for (double& v : p->prof) v = 0.0;
   if (S.dmax > 256) return p->fail(LREP_ERR_ARG, "window + 2*block exceeds 256 columns");
   if (S.nb > 64) return p->fail(LREP_ERR_ARG, "block exceeds 64");

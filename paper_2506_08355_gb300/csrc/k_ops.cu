@@ -17,32 +17,53 @@ namespace lrep {
 namespace {
 
 // ------------------------------------------------------------- stencil
-// Y = coef * Lap_h X + d .* X, zero values outside the grid.  One thread per
-// grid point, blockIdx.y = column; x-neighbours are coalesced, y/z
-// neighbours come from L1/L2 (the planes of a column stay cache-resident).
-__global__ void __launch_bounds__(256)
+// Y = coef * Lap_h X + d .* X, zero values outside the grid.  2.5-D
+// blocking: a CTA owns a 32 x 8 tile of one xy plane of one column and
+// marches along z over a chunk of planes; the z-1 / z+1 neighbours stay in
+// registers and the current plane (with a one-point halo) is staged in
+// shared memory, so each value is read from memory about once.
+constexpr int STX = 32, STY = 8;
+
+__global__ void __launch_bounds__(STX * STY)
 stencil_kernel(int nx, int ny, int nz, double coef, const double* __restrict__ d,
                const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
-               int64_t ldy, const int* __restrict__ skip) {
+               int64_t ldy, int zchunk, int tiles_x, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  const int64_t n = (int64_t)nx * ny * nz;
+  __shared__ double s[STY + 2][STX + 2];
+  const int tx = threadIdx.x % STX, ty = threadIdx.x / STX;
+  const int tile = blockIdx.x;
+  const int i0 = (tile % tiles_x) * STX, j0 = (tile / tiles_x) * STY;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool in = (i < nx) && (j < ny);
+  const int z0 = blockIdx.y * zchunk;
+  const int z1 = min(nz, z0 + zchunk);
   const int64_t plane = (int64_t)nx * ny;
-  const double* x = X + (int64_t)blockIdx.y * ldx;
-  double* y = Y + (int64_t)blockIdx.y * ldy;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(p % nx);
-    const int j = (int)((p / nx) % ny);
-    const int k = (int)(p / plane);
-    const double c = x[p];
-    double s = -6.0 * c;
-    if (i > 0) s += x[p - 1];
-    if (i < nx - 1) s += x[p + 1];
-    if (j > 0) s += x[p - nx];
-    if (j < ny - 1) s += x[p + nx];
-    if (k > 0) s += x[p - plane];
-    if (k < nz - 1) s += x[p + plane];
-    y[p] = fma(coef, s, d[p] * c);
+  const double* x = X + (int64_t)blockIdx.z * ldx;
+  double* y = Y + (int64_t)blockIdx.z * ldy;
+  const int64_t p0 = (int64_t)j * nx + i;
+  double below = (in && z0 > 0) ? x[p0 + (int64_t)(z0 - 1) * plane] : 0.0;
+  double cur = (in && z0 < nz) ? x[p0 + (int64_t)z0 * plane] : 0.0;
+  for (int z = z0; z < z1; ++z) {
+    const int64_t pz = (int64_t)z * plane;
+    const double above = (in && z + 1 < nz) ? x[p0 + pz + plane] : 0.0;
+    s[ty + 1][tx + 1] = cur;
+    // halo: left/right columns by the first/last lane of each row, top/
+    // bottom rows by the first/last warp
+    if (tx == 0) s[ty + 1][0] = (i0 > 0 && j < ny) ? x[pz + (int64_t)j * nx + i0 - 1] : 0.0;
+    if (tx == STX - 1)
+      s[ty + 1][STX + 1] = (i0 + STX < nx && j < ny) ? x[pz + (int64_t)j * nx + i0 + STX] : 0.0;
+    if (ty == 0) s[0][tx + 1] = (j0 > 0 && i < nx) ? x[pz + (int64_t)(j0 - 1) * nx + i] : 0.0;
+    if (ty == STY - 1)
+      s[STY + 1][tx + 1] = (j0 + STY < ny && i < nx) ? x[pz + (int64_t)(j0 + STY) * nx + i] : 0.0;
+    __syncthreads();
+    if (in) {
+      const double lap = s[ty + 1][tx] + s[ty + 1][tx + 2] + s[ty][tx + 1] + s[ty + 2][tx + 1] +
+                         below + above - 6.0 * cur;
+      y[p0 + pz] = fma(coef, lap, d[p0 + pz] * cur);
+    }
+    __syncthreads();
+    below = cur;
+    cur = above;
   }
 }
 
@@ -201,11 +222,15 @@ cudaError_t stencil_apply_f64(int nx, int ny, int nz, double coef_h2,
                               int64_t ldx, double* Y, int64_t ldy,
                               const int* skip, cudaStream_t st) {
   if (c <= 0) return cudaSuccess;
-  const int64_t n = (int64_t)nx * ny * nz;
-  const unsigned gx = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((n + 255) / 256, 8 * kNumSMs));
-  stencil_kernel<<<dim3(gx, c), 256, 0, st>>>(nx, ny, nz, coef_h2, d, X, ldx, Y,
-                                             ldy, skip); LREP_COUNT_LAUNCH();
+  const int tiles_x = (nx + STX - 1) / STX, tiles_y = (ny + STY - 1) / STY;
+  const int tiles = tiles_x * tiles_y;
+  // z chunks: enough CTAs for ~4 per SM over all columns, >= 8 planes each
+  int zchunks = (int)std::max<int64_t>(1, (4 * kNumSMs + (int64_t)tiles * c - 1) / ((int64_t)tiles * c));
+  zchunks = std::min(zchunks, std::max(1, nz / 8));
+  const int zchunk = (nz + zchunks - 1) / zchunks;
+  zchunks = (nz + zchunk - 1) / zchunk;
+  stencil_kernel<<<dim3(tiles, zchunks, c), STX * STY, 0, st>>>(
+      nx, ny, nz, coef_h2, d, X, ldx, Y, ldy, zchunk, tiles_x, skip); LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

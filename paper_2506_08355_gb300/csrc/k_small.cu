@@ -69,7 +69,10 @@ __device__ bool chol_lower(double* L, int d, int* s_flag) {
   return true;
 }
 
-__device__ void small_lrep_body(const SmallJob& J) {
+// The four d x d work matrices live in dynamic shared memory when they fit
+// (d <= 84 with the full 227 KB), else G and V do (d <= 118), else all in
+// the global work array.
+__device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
   const int d = J.d;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -79,10 +82,15 @@ __device__ void small_lrep_body(const SmallJob& J) {
   __shared__ double sig[SMALL_MAXD];
   __shared__ int perm[SMALL_MAXD];
   __shared__ int flip[SMALL_MAXD];
-  double* L1 = J.work;
-  double* L2 = L1 + (size_t)d * d;
-  double* G = L2 + (size_t)d * d;
-  double* V = G + (size_t)d * d;
+  const size_t dd = (size_t)d * d;
+  double *L1, *L2, *G, *V;
+  if (4 * dd * sizeof(double) <= (size_t)dyn_bytes) {
+    L1 = dyn; L2 = dyn + dd; G = dyn + 2 * dd; V = dyn + 3 * dd;
+  } else if (2 * dd * sizeof(double) <= (size_t)dyn_bytes) {
+    L1 = J.work; L2 = J.work + dd; G = dyn; V = dyn + dd;
+  } else {
+    L1 = J.work; L2 = L1 + dd; G = L2 + dd; V = G + dd;
+  }
   if (tid == 0) s_flag = 0;
   // biorthogonality of the current basis (safeguard input)
   if (J.S) {
@@ -119,9 +127,13 @@ __device__ void small_lrep_body(const SmallJob& J) {
   __syncthreads();
   // one-sided Jacobi on the columns of G (G V -> W S)
   const int dp = d + (d & 1), m = dp - 1;
-  const double tol = 4.0 * 2.220446049250313e-16 * sqrt((double)d);
-  int converged = 0;
-  for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
+  // rotate while the columns' cosine exceeds d * eps: above the rounding
+  // floor of the computed inner products (|fl(g_a^T g_b) - g_a^T g_b| <=
+  // d u ||g_a|| ||g_b||), so a sweep without rotation is reached
+  const double tol = (double)d * 2.220446049250313e-16;
+  int converged = 0, sweeps = 0;
+  for (int sweep = 0; sweep < 40 && !converged; ++sweep) {
+    ++sweeps;
     if (tid == 0) s_conv = 1;
     __syncthreads();
     for (int r = 0; r < m; ++r) {
@@ -197,16 +209,36 @@ __device__ void small_lrep_body(const SmallJob& J) {
       J.Yh[r + (size_t)i * J.ldo] = -J.Yh[r + (size_t)i * J.ldo];
     }
   }
-  if (tid == 0) *J.info = converged ? 0 : 3;
+  if (tid == 0) {
+    *J.info = converged ? 0 : 3;
+    if (J.sweeps) *J.sweeps = sweeps;
+  }
 }
 
-__global__ void __launch_bounds__(SMALL_T) small_lrep_kernel(const SmallJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(SMALL_T) small_lrep_kernel(const SmallJob* __restrict__ jobs,
+                                                             int dyn_bytes) {
+  extern __shared__ double dyn[];
   const SmallJob J = jobs[blockIdx.x];
-  small_lrep_body(J);
+  small_lrep_body(J, dyn, dyn_bytes);
 }
 
-__global__ void __launch_bounds__(SMALL_T) small_lrep_one_kernel(SmallJob J) {
-  small_lrep_body(J);
+__global__ void __launch_bounds__(SMALL_T) small_lrep_one_kernel(SmallJob J, int dyn_bytes) {
+  extern __shared__ double dyn[];
+  small_lrep_body(J, dyn, dyn_bytes);
+}
+
+constexpr int kSmallDynBytes = 220 * 1024;
+
+cudaError_t small_smem_setup() {
+  static const cudaError_t once = [] {
+    cudaError_t e = cudaFuncSetAttribute(
+        small_lrep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallDynBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(small_lrep_one_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallDynBytes);
+    return e;
+  }();
+  return once;
 }
 
 // ---------------------------------------------------------------- eq. hat_pq
@@ -302,20 +334,34 @@ __global__ void __launch_bounds__(256) small_pq_kernel(PqJob J) {
 }
 
 // ------------------------------------------------- Alg. 1, coefficient form
+// The coefficient vectors and the Sxy block live in dynamic shared memory
+// when 5 m^2 + 3 m doubles fit (m <= 67), else in the global work array.
 __global__ void __launch_bounds__(512)
 biorth_coef_kernel(int m, const double* __restrict__ G2, int ld2,
                    const double* __restrict__ refw2, const double* __restrict__ refz2,
                    double tau, double* __restrict__ A, double* __restrict__ B, int ldc,
-                   double* __restrict__ work, int* __restrict__ count) {
+                   double* __restrict__ work, int* __restrict__ count, int dyn_bytes) {
   extern __shared__ double sh[];
+  const size_t mm = (size_t)m * m;
+  const bool in_smem = (5 * mm + 3 * (size_t)m) * sizeof(double) <= (size_t)dyn_bytes;
   double* a = sh;          // m
   double* b = a + m;       // m
   double* u = b + m;       // m
+  double *Uc, *Vc, *Ac, *Bc, *S;
+  int lda;
+  if (in_smem) {
+    Uc = u + m; Vc = Uc + mm; Ac = Vc + mm; Bc = Ac + mm; S = Bc + mm; lda = m;
+  } else {
+    Uc = work; Vc = Uc + mm; Ac = A; Bc = B; S = nullptr; lda = ldc;
+  }
   __shared__ int s_kept, s_take;
-  double* Uc = work;                 // m x m: u_j = Sxy b_j
-  double* Vc = Uc + (size_t)m * m;   // m x m: v_j = Sxy^T a_j
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
-#define SXY(t, s) G2[(t) + (size_t)(m + (s)) * ld2]
+  if (in_smem)
+    for (int e = tid; e < (int)mm; e += nt) {
+      const int t = e % m, k = e / m;
+      S[e] = G2[t + (size_t)(m + k) * ld2];
+    }
+#define SXY(t, k) (in_smem ? S[(t) + (size_t)(k) * m] : G2[(t) + (size_t)(m + (k)) * ld2])
   if (tid == 0) s_kept = 0;
   __syncthreads();
   for (int l = 0; l < m; ++l) {
@@ -327,19 +373,19 @@ biorth_coef_kernel(int m, const double* __restrict__ G2, int ld2,
         double r = 0.0;
         for (int i = lane; i < m; i += 32) r = fma(Uc[i + (size_t)j * m], a[i], r);
         r = warp_sum(r);
-        for (int i = lane; i < m; i += 32) a[i] = fma(-r, A[i + (size_t)j * ldc], a[i]);
-        double s = 0.0;
-        for (int i = lane; i < m; i += 32) s = fma(Vc[i + (size_t)j * m], b[i], s);
-        s = warp_sum(s);
-        for (int i = lane; i < m; i += 32) b[i] = fma(-s, B[i + (size_t)j * ldc], b[i]);
+        for (int i = lane; i < m; i += 32) a[i] = fma(-r, Ac[i + (size_t)j * lda], a[i]);
+        double s2 = 0.0;
+        for (int i = lane; i < m; i += 32) s2 = fma(Vc[i + (size_t)j * m], b[i], s2);
+        s2 = warp_sum(s2);
+        for (int i = lane; i < m; i += 32) b[i] = fma(-s2, Bc[i + (size_t)j * lda], b[i]);
         __syncwarp();
       }
     }
     __syncthreads();
     for (int t = tid; t < m; t += nt) {
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s = fma(SXY(t, k), b[k], s);
-      u[t] = s;
+      double acc = 0.0;
+      for (int k = 0; k < m; ++k) acc = fma(SXY(t, k), b[k], acc);
+      u[t] = acc;
     }
     __syncthreads();
     if (tid < 32) {
@@ -356,8 +402,8 @@ biorth_coef_kernel(int m, const double* __restrict__ G2, int ld2,
           a[i] /= rr;
           b[i] /= root;
           u[i] /= root;
-          A[i + (size_t)kept * ldc] = a[i];
-          B[i + (size_t)kept * ldc] = b[i];
+          Ac[i + (size_t)kept * lda] = a[i];
+          Bc[i + (size_t)kept * lda] = b[i];
           Uc[i + (size_t)kept * m] = u[i];
         }
       }
@@ -365,10 +411,10 @@ biorth_coef_kernel(int m, const double* __restrict__ G2, int ld2,
     }
     __syncthreads();
     if (s_take) {
-      for (int s = tid; s < m; s += nt) {
+      for (int s3 = tid; s3 < m; s3 += nt) {
         double v = 0.0;
-        for (int t = 0; t < m; ++t) v = fma(SXY(t, s), a[t], v);
-        Vc[s + (size_t)kept * m] = v;
+        for (int t = 0; t < m; ++t) v = fma(SXY(t, s3), a[t], v);
+        Vc[s3 + (size_t)kept * m] = v;
       }
       __syncthreads();
       if (tid == 0) s_kept = kept + 1;
@@ -376,12 +422,13 @@ biorth_coef_kernel(int m, const double* __restrict__ G2, int ld2,
     __syncthreads();
   }
 #undef SXY
-  // zero the unused coefficient columns
   const int kept = s_kept;
-  for (int e = tid; e < m * (m - kept); e += nt) {
-    const int i = e % m, j = kept + e / m;
-    A[i + (size_t)j * ldc] = 0.0;
-    B[i + (size_t)j * ldc] = 0.0;
+  for (int e = tid; e < (int)mm; e += nt) {
+    const int i = e % m, j = e / m;
+    const double va = (j < kept) ? Ac[i + (size_t)j * lda] : 0.0;
+    const double vb = (j < kept) ? Bc[i + (size_t)j * lda] : 0.0;
+    A[i + (size_t)j * ldc] = va;
+    B[i + (size_t)j * ldc] = vb;
   }
   if (tid == 0) *count = kept;
 }
@@ -441,13 +488,17 @@ size_t small_work_elems(int d) { return (size_t)4 * d * d; }
 
 cudaError_t small_lrep_batched(const SmallJob* jobs_dev, int njobs, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
-  small_lrep_kernel<<<njobs, SMALL_T, 0, st>>>(jobs_dev); LREP_COUNT_LAUNCH();
+  cudaError_t e = small_smem_setup();
+  if (e != cudaSuccess) return e;
+  small_lrep_kernel<<<njobs, SMALL_T, kSmallDynBytes, st>>>(jobs_dev, kSmallDynBytes); LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
 cudaError_t small_lrep_one(const SmallJob& job, cudaStream_t st) {
   if (job.d <= 0 || job.d > SMALL_MAXD) return cudaErrorInvalidValue;
-  small_lrep_one_kernel<<<1, SMALL_T, 0, st>>>(job); LREP_COUNT_LAUNCH();
+  cudaError_t e = small_smem_setup();
+  if (e != cudaSuccess) return e;
+  small_lrep_one_kernel<<<1, SMALL_T, kSmallDynBytes, st>>>(job, kSmallDynBytes); LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -465,10 +516,13 @@ cudaError_t biorth_coef(int m, const double* G2, int ld2, const double* ref_w2,
                         const double* ref_z2, double tau, double* A, double* B,
                         int ldc, double* work, int* count, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
-  const size_t shm = (size_t)3 * m * sizeof(double);
-  if (shm > 48 * 1024) return cudaErrorInvalidValue;
-  biorth_coef_kernel<<<1, 512, shm, st>>>(m, G2, ld2, ref_w2, ref_z2, tau, A, B,
-                                          ldc, work, count); LREP_COUNT_LAUNCH();
+  constexpr int kCoefDyn = 200 * 1024;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      biorth_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCoefDyn);
+  if (attr != cudaSuccess) return attr;
+  if ((size_t)3 * m * sizeof(double) > (size_t)kCoefDyn) return cudaErrorInvalidValue;
+  biorth_coef_kernel<<<1, 512, kCoefDyn, st>>>(m, G2, ld2, ref_w2, ref_z2, tau, A, B,
+                                               ldc, work, count, kCoefDyn); LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

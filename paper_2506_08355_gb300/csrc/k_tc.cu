@@ -264,15 +264,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encoder() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  static const EncodeTiledFn fn = [] {
     cudaDriverEntryPointQueryResult q;
     void* p = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
+      return (EncodeTiledFn)p;
+    return (EncodeTiledFn) nullptr;
+  }();
   return fn;
 }
 
@@ -341,12 +341,9 @@ cudaError_t tc_apply(const TcOperand& A, int64_t n, int c, const double* X, int6
   const int tile_x = N * BK * 2;
   const int stage_bytes = ((2 * TILE_A + 2 * tile_x) + 1023) & ~1023;
   const size_t smem = (size_t)STAGES * stage_bytes + 1024 + 256;
-  static int configured = 0;
-  if (configured < (int)smem) {
-    e = cudaFuncSetAttribute(bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = (int)smem;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (attr != cudaSuccess) return attr;
   dim3 grid((unsigned)((n + BM - 1) / BM), (unsigned)s);
   bf16x3_kernel<<<grid, 128, smem, st>>>(A.hi_map, A.lo_map, mxh, mxl, (int)n, c, N, per, kt,
                                          tcols, part, err, skip); LREP_COUNT_LAUNCH();

@@ -120,6 +120,7 @@ struct SmallJob {
   double* biorth_err;   // max |S - I| (when S given)
   int d;
   int w_prev;           // sign alignment of pairs j < w_prev (reading)
+  int* sweeps = nullptr; // optional: Jacobi sweeps used
 };
 size_t small_work_elems(int d);
 cudaError_t small_lrep_batched(const SmallJob* jobs_dev, int njobs, cudaStream_t st);

@@ -117,7 +117,17 @@ lrep_status apply_op_cg(lrep_problem p, int which, int c, const double* X,
                         double* ws, size_t ws_elems);
 size_t apply_ws_elems(lrep_problem p, int c);
 size_t apply_cg_ws_elems(lrep_problem p, int c);
-lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol);
+// Cross-solve batching of the small projected problems (serving): when
+// given, the solver hands each small LREP to the batcher instead of
+// launching it; the batcher orders the caller's stream after the launch.
+struct SmallBatcher {
+  virtual ~SmallBatcher() {}
+  virtual cudaError_t run(const SmallJob& job, cudaStream_t st) = 0;
+};
+lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol,
+                       SmallBatcher* batcher = nullptr);
+// device bytes the solver's workspace needs for (nev, nb) on p
+size_t bosp_footprint(lrep_problem p, int nev, int nb);
 // mixed precision: build the bf16 hi/lo split of the dense operator
 lrep_status build_split(lrep_problem p);
 void free_split(lrep_problem p);

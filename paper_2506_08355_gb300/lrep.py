@@ -61,11 +61,13 @@ EXPORTS = {
     "lrep_query": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32]),
     "lrep_last_error": (C.c_char_p, [C.c_void_p]),
     "lrep_destroy": (C.c_int, [C.c_void_p]),
+    "lrep_footprint": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]),
     "lrep_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int64, C.c_int32, C.c_void_p]),
     "lrep_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                      C.c_double, C.POINTER(C.c_uint64)]),
     "lrep_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32]),
     "lrep_server_destroy": (C.c_int, [C.c_void_p]),
+    "lrep_server_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lrep_op_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
                                 C.c_void_p, C.c_int64]),
     "lrep_op_apply_cg": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
@@ -327,6 +329,12 @@ class Problem:
     def rebiorths(self):
         return self._q_scalar(Q_REBIORTHS, C.c_int32)
 
+    def footprint(self, nev, block):
+        """Device bytes a solve needs beyond the operator (server admission)."""
+        v = C.c_int64()
+        _check(lib().lrep_footprint(self.h, nev, block, C.byref(v)), self.h)
+        return v.value
+
     def profile(self):
         """(product seconds, product launches, flops, algorithmic bytes)."""
         return self._q_array(Q_PROFILE, 4)
@@ -421,11 +429,18 @@ class Server:
 
     def submit(self, problem, nev, block, tol):
         t = C.c_uint64()
-        _check(lib().lrep_server_submit(self.h, problem.h, nev, block, tol, C.byref(t)))
+        _check(lib().lrep_server_submit(self.h, problem.h, nev, block, tol, C.byref(t)),
+               problem.h)
         return t.value
 
     def wait(self, ticket, timeout_ms=-1):
         return lib().lrep_server_wait(self.h, ticket, timeout_ms)
+
+    def stats(self):
+        """(batched small-LREP launches, problems in them, largest batch)."""
+        out = np.zeros(3, dtype=np.int64)
+        _check(lib().lrep_server_stats(self.h, _ptr(out)))
+        return tuple(int(v) for v in out)
 
     def close(self):
         if self.h:

@@ -58,6 +58,27 @@ def config1_r2():
     print(path)
 
 
+def config2_r2():
+    """Oracle R2 (literal Alg. 2) on the 64^3 BdG-like stencil workload:
+    n = 262144, nev = 32, nb = 16, tol 1e-10, nullspace phi."""
+    import time
+    p = synth.config(2)
+    op = R.StencilOp(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"], p["dM"])
+    t0 = time.perf_counter()
+    res = R.bosp(op, p["nev"], p["block"], p["tol"], X0=p["X0"])
+    dt = time.perf_counter() - t0
+    path = os.path.join(HERE, "config2_oracle_run.txt")
+    with open(path, "w") as f:
+        f.write("# oracle R2 (literal Alg. 2, numpy FP64) on synth.config(2):\n"
+                "# 64^3 BdG-like 7-point stencil, nev = 32, nb = 16, tol 1e-10,\n"
+                "# nullspace phi; written by tests/golden/make_golden.py config2_r2\n")
+        f.write("iters %d\nmatvecs %d\nconverged %d\nrebiorths %d\nseconds %.1f\n"
+                % (res.iters, res.matvecs, int(res.converged), res.rebiorths, dt))
+        for v in res.lam:
+            f.write("lam %.17e\n" % v)
+    print(path)
+
+
 if __name__ == "__main__":
     for name in sys.argv[1:] or ["config1"]:
         globals()[name]()

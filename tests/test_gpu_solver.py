@@ -224,3 +224,36 @@ def test_mixed_precision_config0_and_moving(L):
     assert prob.solve(64, 16, 1e-10) == L.OK
     check(R.DenseOp(q["K"], q["M"]), prob, lam_r, 1e-10, 64)
     prob.close()
+
+
+def _stored_run(name):
+    lam = []
+    meta = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        if line.startswith("#"):
+            continue
+        k, v = line.split()
+        if k == "lam":
+            lam.append(float(v))
+        else:
+            meta[k] = float(v)
+    return np.array(lam), meta
+
+
+def test_full_size_stencil_64cubed_fp64(L):
+    """The 64^3 BdG-like stencil workload (n = 262144, nev 32, block 16,
+    tol 1e-10, nullspace phi): eigenvalues against the oracle's literal
+    Alg. 2 run (stored), residuals and biorthogonality re-checked on the
+    CPU for every returned pair, deflation against V0."""
+    gold = os.path.join(os.path.dirname(__file__), "golden", "config2_oracle_run.txt")
+    if not os.path.exists(gold):
+        pytest.skip("stored oracle run missing")
+    lam_ref, meta = _stored_run("config2_oracle_run.txt")
+    p = synth.config(2)
+    op = R.StencilOp(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"], p["dM"])
+    prob = L.Problem.stencil(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"], p["dM"])
+    prob.set_nullspace(p["X0"])
+    assert prob.solve(32, 16, 1e-10) == L.OK
+    lam, X, Y = check(op, prob, lam_ref, 1e-10, 32, rtol=1e-10)
+    assert np.abs(p["X0"][:, 0] @ Y).max() < 1e-9
+    prob.close()
