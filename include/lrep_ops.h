@@ -86,6 +86,32 @@ lrep_status lrep_op_philox_normal(int64_t n, int32_t ncols, uint64_t seed,
                                   int32_t stream_id, double* out, int64_t ld,
                                   void* stream);
 
+/* Tall-skinny Gram G = A^T B exactly like lrep_op_gram, but without any
+ * device allocation, for callers that cannot allocate device memory at the
+ * time of the call: processes whose HBM was reserved up front by another
+ * allocator (cudaMalloc could fail), or latency-critical loops that cannot
+ * accept cudaMalloc/cudaFree stalls.  The paper has no counterpart; this is
+ * a deployment variant of the Gram step.
+ *  - Scratch: a fixed array of 2^19 doubles (4 MiB) in device memory that is
+ *    part of the library image; every GPU that loads the library holds it
+ *    until the process exits.  Limit: a * b <= LREP_GRAM_NOALLOC_MAX_AB
+ *    (65536); larger requests return LREP_ERR_ARG with a message in
+ *    lrep_last_error(NULL).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the array and leaves its partials there; nothing in
+ *    it needs to start at zero (each call overwrites what it reads).  Calls
+ *    that overlap on the GPU (different streams, or different host threads)
+ *    race on the array: serialise them.
+ *  - Asynchronous on `stream`; results may differ from lrep_op_gram in the
+ *    last bits (the split of the reduction over rows may be coarser). */
+#define LREP_GRAM_NOALLOC_MAX_AB 65536
+lrep_status lrep_op_gram_noalloc(int64_t n, int32_t a, int32_t b,
+                                 const double* A, int64_t lda, const double* B,
+                                 int64_t ldb, double* G, int64_t ldg,
+                                 void* stream);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all problems); a monotone counter for accounting. */
 int64_t lrep_launch_count(void);

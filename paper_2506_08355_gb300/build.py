@@ -22,7 +22,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblrep.so")
 
 SOURCES = ["k_blas.cu", "k_small.cu", "k_ops.cu", "k_tc.cu", "mixed.cu",
-           "bosp.cu", "capi.cu", "server.cu"]
+           "bosp.cu", "capi.cu", "server.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-I", INCLUDE, "--expt-relaxed-constexpr"]

@@ -105,6 +105,7 @@ lrep_status pool_take(size_t elems, double** out) {
 }  // namespace
 
 namespace lrep {
+void set_global_error(const char* msg) { g_err = msg; }
 lrep_status apply_op_cg(lrep_problem p, int which, int c, const double* X,
                         int64_t ldx, double* Y, int64_t ldy, const int* skip,
                         double* ws, size_t ws_elems);

@@ -242,6 +242,28 @@ cudaError_t gram_f64(int64_t n, const Segs& A, const Segs& B, double* G,
   return cudaGetLastError();
 }
 
+// Same Gram with the number of row slabs capped (for a fixed-size caller
+// scratch of ws_elems doubles); fewer slabs change only the summation
+// partition.
+cudaError_t gram_f64_capped(int64_t n, const Segs& A, const Segs& B, double* G,
+                            int64_t ldg, double* ws, size_t ws_elems, cudaStream_t st) {
+  const int a = A.total(), b = B.total();
+  if (a <= 0 || b <= 0) return cudaSuccess;
+  const size_t ab = (size_t)a * b;
+  if (ws_elems < ab) return cudaErrorInvalidValue;
+  int slabs = gram_slabs(n, a, b);
+  slabs = (int)std::min<size_t>((size_t)slabs, ws_elems / ab);
+  int64_t slab_rows = (n + slabs - 1) / slabs;
+  slab_rows = std::max<int64_t>(((slab_rows + GK - 1) / GK) * GK, GK);
+  slabs = (int)std::max<int64_t>((n + slab_rows - 1) / slab_rows, 1);
+  const int tiles_b = (b + GT - 1) / GT;
+  const int tiles = ((a + GT - 1) / GT) * tiles_b;
+  gram_kernel<<<dim3(tiles, slabs), 256, 0, st>>>(n, A, B, a, b, tiles_b, slab_rows, ws); LREP_COUNT_LAUNCH();
+  const int blocks = (int)std::min<int64_t>(((int64_t)ab + 255) / 256, 4 * kNumSMs);
+  gram_reduce_kernel<<<blocks, 256, 0, st>>>(a, b, slabs, ws, G, ldg); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
 // =====================================================================
 // Block update C = alpha C + beta A B, A n x k (segmented), B k x c.
 // CTA = 64 rows x 32 columns; 256 threads: row = t % 64, 8 columns each.

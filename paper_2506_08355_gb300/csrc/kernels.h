@@ -35,6 +35,10 @@ size_t gram_ws_elems(int64_t n, int a, int b);
 cudaError_t gram_f64(int64_t n, const Segs& A, const Segs& B, double* G,
                      int64_t ldg, double* ws, size_t ws_elems, cudaStream_t st);
 
+// Gram with the slab count capped to fit ws_elems (>= a*b) doubles.
+cudaError_t gram_f64_capped(int64_t n, const Segs& A, const Segs& B, double* G,
+                            int64_t ldg, double* ws, size_t ws_elems, cudaStream_t st);
+
 // C (n x c) = alpha C + beta A B, A segmented (k columns), B k x c (ldb).
 cudaError_t update_f64(int64_t n, int c, double alpha, const Segs& A,
                        const double* B, int64_t ldb, double beta, double* C,

@@ -89,6 +89,9 @@ EXPORTS = {
     "lrep_op_philox_normal": (C.c_int, [C.c_int64, C.c_int32, C.c_uint64, C.c_int32,
                                         C.c_void_p, C.c_int64, C.c_void_p]),
     "lrep_launch_count": (C.c_int64, []),
+    "lrep_op_gram_noalloc": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                       C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                       C.c_void_p]),
 }
 
 _lib = None
