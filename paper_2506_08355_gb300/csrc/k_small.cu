@@ -69,9 +69,54 @@ __device__ bool chol_lower(double* L, int d, int* s_flag) {
   return true;
 }
 
-// The four d x d work matrices live in dynamic shared memory when they fit
-// (d <= 84 with the full 227 KB), else G and V do (d <= 118), else all in
-// the global work array.
+// ---------------------------------------------------------------- small LREP
+// FP64 is scarce on GB300 (about 2 FMA per clock per SM), so the SVD of
+// G = L1^T L2 runs in two phases inside the CTA:
+//  1. one-sided (Hestenes) Jacobi in FP32 on a copy of G, round-robin pair
+//     order, until every column pair's cosine is below 2 sqrt(d) eps_32;
+//  2. FP64 refinement of the right factor V by matrix products: two
+//     Newton-Schulz steps V <- V - V (V^T V - I)/2, then steps of
+//     simultaneous Jacobi rotations B = G V, C = B^T B, t_ab from the 2 x 2
+//     problem of columns (a, b), V <- V (I + T - T^T), each followed by one
+//     Newton-Schulz step, until max cos < d eps (quadratic convergence).
+// The column products of B keep each pair's rounding relative to
+// sigma_a sigma_b, so small singular values keep relative accuracy.
+// dyn: dynamic shared memory (dyn_bytes); matrices are column-major with
+// leading dimension d.
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// C = A * B (+ beta C) for d x d column-major matrices (ld d); C must not
+// alias A or B.  transA: use A^T.
+__device__ void mm_d(int d, const double* A, bool transA, const double* B, double* C,
+                     double alpha, double beta) {
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+    const int i = e % d, j = e / d;
+    double s = 0.0;
+    if (transA)
+      for (int k = 0; k < d; ++k) s = fma(A[k + i * d], B[k + j * d], s);
+    else
+      for (int k = 0; k < d; ++k) s = fma(A[i + k * d], B[k + j * d], s);
+    C[e] = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * C[e]);
+  }
+  __syncthreads();
+}
+
+// Newton-Schulz step: V <- V - V (V^T V - I) / 2, using R and T as scratch.
+__device__ void ns_step(int d, double*& V, double*& T, double* R) {
+  mm_d(d, V, true, V, R, 1.0, 0.0);
+  for (int i = threadIdx.x; i < d; i += blockDim.x) R[i + i * d] -= 1.0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) T[e] = V[e];
+  __syncthreads();
+  mm_d(d, V, false, R, T, -0.5, 1.0);
+  double* t = V; V = T; T = t;
+}
+
 __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
   const int d = J.d;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -83,14 +128,18 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
   __shared__ int perm[SMALL_MAXD];
   __shared__ int flip[SMALL_MAXD];
   const size_t dd = (size_t)d * d;
-  double *L1, *L2, *G, *V;
+  // L1, L2 in the global work array; G, V, B, S (+ float copies) in shared
+  // memory when 4 d^2 doubles fit, else in the work array too.
+  double* L1 = J.work;
+  double* L2 = J.work + dd;
+  double *G, *V, *B, *S;
   if (4 * dd * sizeof(double) <= (size_t)dyn_bytes) {
-    L1 = dyn; L2 = dyn + dd; G = dyn + 2 * dd; V = dyn + 3 * dd;
-  } else if (2 * dd * sizeof(double) <= (size_t)dyn_bytes) {
-    L1 = J.work; L2 = J.work + dd; G = dyn; V = dyn + dd;
+    G = dyn; V = dyn + dd; B = dyn + 2 * dd; S = dyn + 3 * dd;
   } else {
-    L1 = J.work; L2 = L1 + dd; G = L2 + dd; V = G + dd;
+    G = J.work + 2 * dd; V = J.work + 3 * dd; B = J.work + 4 * dd; S = J.work + 5 * dd;
   }
+  float* G32 = reinterpret_cast<float*>(B);   // phase 1 aliases B and S
+  float* V32 = reinterpret_cast<float*>(S);
   if (tid == 0) s_flag = 0;
   // biorthogonality of the current basis (safeguard input)
   if (J.S) {
@@ -116,23 +165,21 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
     if (tid == 0) *J.info = 2;
     return;
   }
-  // G = L1^T L2 (both lower triangular), V = I
+  // G = L1^T L2 (both lower triangular)
   for (int e = tid; e < d * d; e += nt) {
     const int i = e % d, j = e / d;
     double s = 0.0;
     for (int k = max(i, j); k < d; ++k) s = fma(L1[k + i * d], L2[k + j * d], s);
     G[e] = s;
-    V[e] = (i == j) ? 1.0 : 0.0;
+    G32[e] = (float)s;
+    V32[e] = (i == j) ? 1.0f : 0.0f;
   }
   __syncthreads();
-  // one-sided Jacobi on the columns of G (G V -> W S)
+  // ---- phase 1: FP32 one-sided Jacobi
   const int dp = d + (d & 1), m = dp - 1;
-  // rotate while the columns' cosine exceeds d * eps: above the rounding
-  // floor of the computed inner products (|fl(g_a^T g_b) - g_a^T g_b| <=
-  // d u ||g_a|| ||g_b||), so a sweep without rotation is reached
-  const double tol = (double)d * 2.220446049250313e-16;
-  int converged = 0, sweeps = 0;
-  for (int sweep = 0; sweep < 40 && !converged; ++sweep) {
+  const float tol32 = 2.0f * sqrtf((float)d) * 1.1920929e-7f;
+  int sweeps = 0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
     ++sweeps;
     if (tid == 0) s_conv = 1;
     __syncthreads();
@@ -143,36 +190,90 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
         else { a = (r + p) % m; b = (r - p + m) % m; }
         if (a > b) { const int t = a; a = b; b = t; }
         if (b >= d) continue;
-        double al = 0.0, be = 0.0, ga = 0.0;
+        float al = 0.f, be = 0.f, ga = 0.f;
         for (int i = lane; i < d; i += 32) {
-          const double x = G[i + a * d], y = G[i + b * d];
-          al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+          const float x = G32[i + a * d], y = G32[i + b * d];
+          al = fmaf(x, x, al); be = fmaf(y, y, be); ga = fmaf(x, y, ga);
         }
-        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (fabs(ga) > tol * sqrt(al * be)) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        al = warp_sumf(al); be = warp_sumf(be); ga = warp_sumf(ga);
+        if (fabsf(ga) > tol32 * sqrtf(al * be)) {
+          const float zeta = (be - al) / (2.0f * ga);
+          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float c = rsqrtf(1.f + t * t), s = c * t;
           for (int i = lane; i < d; i += 32) {
-            const double x = G[i + a * d], y = G[i + b * d];
-            G[i + a * d] = c * x - s * y;
-            G[i + b * d] = s * x + c * y;
-            const double u = V[i + a * d], v = V[i + b * d];
-            V[i + a * d] = c * u - s * v;
-            V[i + b * d] = s * u + c * v;
+            const float x = G32[i + a * d], y = G32[i + b * d];
+            G32[i + a * d] = c * x - s * y;
+            G32[i + b * d] = s * x + c * y;
+            const float u = V32[i + a * d], v = V32[i + b * d];
+            V32[i + a * d] = c * u - s * v;
+            V32[i + b * d] = s * u + c * v;
           }
           if (lane == 0) s_conv = 0;
         }
       }
       __syncthreads();
     }
-    converged = s_conv;
+    const int conv = s_conv;
     __syncthreads();
+    if (conv) break;
   }
-  // singular values, ascending order (ties by index)
+  // ---- phase 2: FP64 refinement of V
+  for (int e = tid; e < d * d; e += nt) V[e] = (double)V32[e];
+  __syncthreads();
+  ns_step(d, V, B, S);
+  ns_step(d, V, B, S);
+  const double tol = (double)d * 2.220446049250313e-16;
+  int converged = 0;
+  for (int it = 0; it < 6; ++it) {
+    mm_d(d, G, false, V, B, 1.0, 0.0);            // B = G V
+    // S = B^T B (upper part), then rotation parameters in place (upper)
+    double cmax = 0.0;
+    for (int e = tid; e < d * d; e += nt) {
+      const int i = e % d, j = e / d;
+      if (i > j) continue;
+      double s = 0.0;
+      for (int k = 0; k < d; ++k) s = fma(B[k + i * d], B[k + j * d], s);
+      S[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < d * d; e += nt) {
+      const int i = e % d, j = e / d;
+      if (i >= j) continue;
+      const double aa = S[i + i * d], bb = S[j + j * d], g = S[e];
+      cmax = fmax(cmax, fabs(g) / sqrt(aa * bb));
+    }
+    cmax = block_max(cmax, red);
+    if (cmax <= tol) {
+      converged = 1;
+      break;
+    }
+    // Omega = T - T^T into the lower/upper of S (diagonal 0)
+    for (int e = tid; e < d * d; e += nt) {
+      const int i = e % d, j = e / d;
+      if (i >= j) continue;
+      const double aa = S[i + i * d], bb = S[j + j * d], g = S[e];
+      double t = 0.0;
+      if (g != 0.0) {
+        const double zeta = (bb - aa) / (2.0 * g);
+        t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      }
+      S[e] = t;  // upper: +t
+      S[j + i * d] = -t;  // lower: -t (distinct element, no race)
+    }
+    __syncthreads();  // the diagonal is still read above
+    for (int i = tid; i < d; i += nt) S[i + i * d] = 0.0;
+    __syncthreads();
+    for (int e = tid; e < d * d; e += nt) B[e] = V[e];
+    __syncthreads();
+    mm_d(d, V, false, S, B, 1.0, 1.0);            // B = V + V Omega
+    { double* t = V; V = B; B = t; }
+    ns_step(d, V, B, S);
+  }
+  if (!converged) mm_d(d, G, false, V, B, 1.0, 0.0);
+  // singular values (column norms of B = G V), ascending order (ties by index)
   for (int j = wid; j < d; j += nw) {
     double s = 0.0;
-    for (int i = lane; i < d; i += 32) s = fma(G[i + j * d], G[i + j * d], s);
+    for (int i = lane; i < d; i += 32) s = fma(B[i + j * d], B[i + j * d], s);
     s = warp_sum(s);
     if (lane == 0) sig[j] = sqrt(s);
   }
@@ -183,7 +284,7 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
     perm[rk] = j;
   }
   __syncthreads();
-  // X^ = L2 V S^-1/2,  Y^ = L1 W S^-1/2 with W = G V / S (G holds G V)
+  // X^ = L2 V S^-1/2,  Y^ = L1 W S^-1/2 with W = B / S
   for (int e = tid; e < d * d; e += nt) {
     const int r = e % d, i = e / d;
     const int j = perm[i];
@@ -191,7 +292,7 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
     double x = 0.0, y = 0.0;
     for (int k = 0; k <= r; ++k) {
       x = fma(L2[r + k * d], V[k + j * d], x);
-      y = fma(L1[r + k * d], G[k + j * d], y);
+      y = fma(L1[r + k * d], B[k + j * d], y);
     }
     J.Xh[r + (size_t)i * J.ldo] = x / sqrt(s);
     J.Yh[r + (size_t)i * J.ldo] = y / (s * sqrt(s));
@@ -484,7 +585,7 @@ cudaError_t chol_upper_inverse(int r, const double* G, int ldg, double* Cinv,
   return cudaGetLastError();
 }
 
-size_t small_work_elems(int d) { return (size_t)4 * d * d; }
+size_t small_work_elems(int d) { return (size_t)6 * d * d; }
 
 cudaError_t small_lrep_batched(const SmallJob* jobs_dev, int njobs, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
