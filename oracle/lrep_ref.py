@@ -321,6 +321,18 @@ def residuals(op, X, Y, lam, KX=None, MY=None):
     return num / den
 
 
+def nullspace_definition(K, tol):
+    """Orthonormal basis of N(K) for symmetric positive semi-definite K, by
+    definition: the eigenvectors of K whose eigenvalues are at most
+    tol * ||K||_2 (the pre-step of the Remark on the numerical computation
+    of the generalized nullspace, which leaves the symmetric eigensolver
+    open).  Returns X0 (n x r) and all eigenvalues ascending."""
+    w, V = np.linalg.eigh(np.asarray(K, dtype=np.float64))
+    nrm = np.abs(w).max() if w.size else 0.0
+    keep = w <= tol * nrm
+    return V[:, keep].copy(), w
+
+
 def setup_nullspace(op, X0, Y0=None, cg_tol=1e-14, cg_maxit=50000):
     """Biorthogonal basis of the generalized nullspace V0.
 

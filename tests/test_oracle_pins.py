@@ -407,3 +407,24 @@ def test_bosp_stencil_separable():
     lam = np.sqrt(kap * (kap + c))[:8]
     res = R.bosp(op, 8, 4, 1e-10, X0=p["phi"][:, None])
     _check_solution(op, res, lam, 1e-10, 8)
+
+
+def test_nullspace_definition_recovers_chosen_kernel():
+    """K = Q diag(k) Q^T with k_0..k_{r-1} = 0: the definition returns a
+    basis of span(Q[:, :r]) (same orthogonal projector) and nothing else;
+    with no zero k it returns an empty basis; a zero matrix is all kernel."""
+    rng = np.random.default_rng(11)
+    n, r = 60, 3
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    k = rng.uniform(0.5, 10.0, n)
+    k[:r] = 0.0
+    K = (Q * k) @ Q.T
+    X0, w = R.nullspace_definition(K, 1e-10)
+    assert X0.shape == (n, r)
+    np.testing.assert_allclose(X0 @ X0.T, Q[:, :r] @ Q[:, :r].T, atol=1e-12)
+    np.testing.assert_allclose(np.sort(w)[r:], np.sort(k[r:]), rtol=1e-12)
+    k[:r] = 1e-3  # smallest eigenvalue 1e-4 of ||K||: not a kernel at tol 1e-10
+    X1, _ = R.nullspace_definition((Q * k) @ Q.T, 1e-10)
+    assert X1.shape == (n, 0)
+    X2, _ = R.nullspace_definition(np.zeros((5, 5)), 1e-10)
+    assert X2.shape == (5, 5)
