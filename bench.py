@@ -2,7 +2,7 @@
 """Throughput of the GB300 BOSP solver: eigenpairs/s at residual <= tol.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision fp64|mixed]
+                    [--precision fp64|mixed|sliced|mixed-sliced]
 
 One step is one complete solve (Alg. 2 with the moving window) of the dense
 n = 8192 workload: K, M built from chosen spectra with Haar bases, k and m
@@ -35,6 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 nominal (unit counts x clock)
+# --precision: the library's precision codes (bit 0: bf16 hi+lo CG operator,
+# bit 1: float64-accurate products by error-free slicing on bf16 tensor cores)
+PRECISIONS = {"fp64": 0, "mixed": 1, "sliced": 2, "mixed-sliced": 3}
+DTYPES = {"fp64": "f64", "mixed": "bf16x3+f64", "sliced": "f64 (bf16 digit slices)",
+          "mixed-sliced": "bf16x3+f64 (bf16 digit slices)"}
 
 
 def parse():
@@ -43,14 +48,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--op", default=None, choices=["dense", "tc", "small", "stencil", "gram"],
+    ap.add_argument("--op", default=None, choices=["dense", "tc", "sliced", "small", "stencil", "gram"],
                     help="time one hot-path step alone (for ncu captures) instead of solves")
     ap.add_argument("--n", type=int, default=8192, help="order for --op")
     ap.add_argument("--cols", type=int, default=16, help="block columns for --op")
     ap.add_argument("--reps", type=int, default=3, help="launches for --op")
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3],
+                    help="1: dense n=8192 (default); 2: 64^3 stencil; 3: dense n=32768")
     ap.add_argument("--serve", action="store_true",
                     help="serving workload: Poisson arrivals through lrep_server_*")
     ap.add_argument("--requests", type=int, default=1000)
@@ -136,8 +143,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload(precision):
+def workload(precision, config=1):
     from paper_2506_08355_gb300 import synth
+    if config == 2:
+        p = synth.config(2)
+        return p, {"workload": "stencil-bdg-64^3-nev32-block16-null1-tol1e-10",
+                   "n": p["n"], "nev": 32, "block": 16, "tol": 1e-10, "nullspace": 1,
+                   "operator": "7-point -1/2 Lap_h + d_K / d_M, Gaussian condensate",
+                   "precision": precision, "window": "moving, s = 3",
+                   "l2": "block of 16 columns (33.5 MB) fits L2; operator is matrix-free"}
+    if config == 3:
+        p = synth.haar_dense_device(32768, seed=3, k_range=(1e-2, 1e2), m_range=(1e-2, 1e2),
+                                    law="loguniform")
+        p.update(nev=256, block=32, tol=1e-8, X0=None)
+        return p, {"workload": "dense-lrep-n32768-nev256-block32-tol1e-8",
+                   "n": 32768, "nev": 256, "block": 32, "tol": 1e-8, "nullspace": 0,
+                   "spectra": "k, m log-uniform [1e-2, 1e2], Haar Q1, Q2 (seed 3, device)",
+                   "precision": precision, "window": "moving, s = 3",
+                   "l2": "operator 17.2 GB resident, larger than L2 (no flush)"}
     p = synth.config(1)
     return p, {"workload": "dense-lrep-n8192-nev64-block16-null4-tol1e-10",
                "n": 8192, "nev": 64, "block": 16, "tol": 1e-10, "nullspace": 4,
@@ -154,7 +177,10 @@ def oracle_sample(p, sample_iters, full_iters):
     iterations on the same workload and scale to a full solve by the
     iteration count of a full solve."""
     from oracle import lrep_ref as R
-    op = R.DenseOp(p["K"], p["M"])
+    if "dK" in p:
+        op = R.StencilOp(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"], p["dM"])
+    else:
+        op = R.DenseOp(p["K"], p["M"])
     t0 = time.perf_counter()
     R.bosp(op, p["nev"], p["block"], p["tol"], X0=p["X0"], max_iters=sample_iters)
     dt = time.perf_counter() - t0
@@ -164,9 +190,9 @@ def oracle_sample(p, sample_iters, full_iters):
     return {"value": p["nev"] / est, "unit": "eigenpairs/s", "cores": cores,
             "kind": "oracle",
             "sample": "numpy FP64 oracle (literal Alg. 2), first %d outer iterations of "
-                      "the same n=8192 workload in %.1f s (%.2f s/iteration, numpy BLAS "
+                      "the same n=%d workload in %.1f s (%.2f s/iteration, numpy BLAS "
                       "threads = cores), scaled to a full solve of %d iterations"
-                      % (sample_iters, dt, per_it, full_iters),
+                      % (sample_iters, op.n, dt, per_it, full_iters),
             "seconds": dt}
 
 
@@ -212,13 +238,15 @@ def op_mode(args):
     g = torch.Generator(device="cuda").manual_seed(0)
     times = []
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    if args.op in ("dense", "tc"):
+    if args.op in ("dense", "tc", "sliced"):
         A = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
         K = (A + A.T) * 0.5
         del A
         p = lrep.Problem.dense(K, K, borrow=True)
         if args.op == "tc":
             p.set_options(precision=lrep.PREC_MIXED_BF16X3)
+        elif args.op == "sliced":
+            p.set_options(precision=lrep.PREC_FP64_SLICED)
         X = torch.randn(c, n, dtype=torch.float64, device="cuda", generator=g)
         Y = torch.empty(c, n, dtype=torch.float64, device="cuda")
         for _ in range(args.reps):
@@ -230,9 +258,13 @@ def op_mode(args):
         ref = (K @ X.T).T
         err = ((Y - ref).abs().max() / (K.abs() @ X.abs().T).max()).item()
         assert err < (1e-4 if args.op == "tc" else 1e-13), err
-        work = {"flops": 2.0 * n * n * c * (3 if args.op == "tc" else 1),
-                "bytes": (4.0 if args.op == "tc" else 8.0) * n * n + 16.0 * n * c,
-                "max_rel_err": err}
+        # tensor-core flops actually issued: 3 bf16 products (tc), the 28
+        # digit-pair products of the sliced emulation; bytes: operator read
+        # once (4, 14 or 8 bytes per entry) plus X and Y
+        mult = {"tc": 3, "sliced": 28, "dense": 1}[args.op]
+        per = {"tc": 4.0, "sliced": 14.0, "dense": 8.0}[args.op]
+        work = {"flops": 2.0 * n * n * c * mult, "fp64_flops": 2.0 * n * n * c,
+                "bytes": per * n * n + 16.0 * n * c, "max_rel_err": err}
         p.close()
     elif args.op == "stencil":
         from paper_2506_08355_gb300 import synth
@@ -404,14 +436,24 @@ def main():
         pg = td
     from paper_2506_08355_gb300 import build, lrep
     build.build()
-    p, cfg = workload(args.precision)
+    p, cfg = workload(args.precision, args.config)
     nev, nb, tol = p["nev"], p["block"], p["tol"]
-    prec = lrep.PREC_FP64 if args.precision == "fp64" else lrep.PREC_MIXED_BF16X3
+    prec = PRECISIONS[args.precision]
     stream = torch.cuda.Stream(device=dev)
-    Kd = torch.from_numpy(p["K"]).to(dev)
-    Md = torch.from_numpy(p["M"]).to(dev)
-    prob = lrep.Problem.dense(Kd, Md, borrow=True, stream=stream)
-    prob.set_nullspace(p["X0"])
+    if args.config == 2:
+        prob = lrep.Problem.stencil(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"],
+                                    p["dM"], stream=stream)
+        args.no_e2e = True
+    else:
+        Kd = p["K"] if not isinstance(p["K"], np.ndarray) else torch.from_numpy(p["K"]).to(dev)
+        Md = p["M"] if not isinstance(p["M"], np.ndarray) else torch.from_numpy(p["M"]).to(dev)
+        prob = lrep.Problem.dense(Kd, Md, borrow=True, stream=stream)
+    if args.config == 3:
+        args.no_e2e = True
+        args.no_cpu = True
+    if p.get("X0") is not None:
+        X0 = p["X0"]
+        prob.set_nullspace(X0 if isinstance(X0, np.ndarray) else X0.T.contiguous())
     prob.set_options(precision=prec, profile=0)
     for _ in range(args.warmup):
         st = prob.solve(nev, nb, tol)
@@ -445,21 +487,38 @@ def main():
     # CUDA events on the solver's stream)
     prob.set_options(precision=prec, profile=1)
     prob.solve(nev, nb, tol)
-    prof = prob.profile()
+    prof_all = np.asarray(prob.profile())
+    prof_cg = np.asarray(prob.profile_cg())
     prob.set_options(precision=prec, profile=0)
+    # the dominant product class by device time: CG-operator products or
+    # the float64-accurate products
+    cg_dominant = prof_cg[0] >= prof_all[0] - prof_cg[0]
+    prof = prof_cg if cg_dominant else prof_all - prof_cg
     launches_p = max(prof[1], 1.0)
     avg_s = prof[0] / launches_p
     flops_launch = prof[2] / launches_p
     bytes_launch = prof[3] / launches_p
     peaks = measured_peaks()
-    roof = {"kernel": "dense_apply_f64 (+ split-K reduce)", "bound": "alu",
+    hbm_peak = peaks.get("hbm_gbs", 6780.7)
+    if args.config == 2:
+        kname = "stencil_kernel (2.5-D)"
+    elif cg_dominant and (prec & lrep.PREC_MIXED_BF16X3):
+        kname = "bf16x3_kernel (+ X split, split-K sum)"
+    elif prec & lrep.PREC_FP64_SLICED:
+        kname = "oz_gemm_kernel (+ X digit planes, split-K sum)"
+    else:
+        kname = "dense_apply_f64 (+ split-K reduce)"
+    hbm_bound = args.config == 2 or not kname.startswith("dense_apply_f64")
+    roof = {"kernel": kname, "bound": "hbm" if hbm_bound else "alu",
             "achieved": flops_launch / avg_s / 1e12, "peak": FP64_PEAK_GFLOPS / 1e3,
             "unit": "TFLOP/s", "frac": (flops_launch / avg_s / 1e9) / FP64_PEAK_GFLOPS,
             "traffic": None, "algorithmic_flops_per_launch": flops_launch,
             "algorithmic_bytes_per_launch": bytes_launch,
             "avg_launch_ms": avg_s * 1e3, "launches_per_solve": prof[1],
+            "product_seconds_per_solve": {"cg_operator": float(prof_cg[0]),
+                                          "float64_products": float(prof_all[0] - prof_cg[0])},
             "hbm_gbs_achieved": bytes_launch / avg_s / 1e9,
-            "hbm_frac_of_measured": (bytes_launch / avg_s / 1e9) / peaks.get("hbm_gbs", 6780.7),
+            "hbm_frac_of_measured": (bytes_launch / avg_s / 1e9) / hbm_peak,
             "peak_note": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak); HBM of measured"}
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -491,12 +550,18 @@ def main():
             cpu = oracle_sample(p, 3, int(np.mean(iters)))
         except Exception as ex:  # reported, not fatal
             cpu = {"error": str(ex)}
+    if hbm_bound:
+        roof["achieved"] = bytes_launch / avg_s / 1e9
+        roof["peak"] = hbm_peak
+        roof["unit"] = "GB/s"
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["peak_note"] = "HBM of measured (MEASURED_PEAKS.json hbm_gbs)"
     if rank == 0:
-        line = {"metric": "eigenpairs/s at residual<=1e-10 (%s path)" % args.precision.upper(),
+        line = {"metric": "eigenpairs/s at residual<=%g (%s path)" % (tol, args.precision.upper()),
                 "value": value, "unit": "eigenpairs/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.precision == "fp64" else "bf16x3+f64",
+                "dtype": DTYPES[args.precision],
                 "data": "synthetic", "config": cfg,
                 "outer_iterations": iters, "max_residual": float(res.max()),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

@@ -60,13 +60,28 @@ enum { LREP_MEM_HOST = 0, LREP_MEM_DEVICE_COPY = 1, LREP_MEM_DEVICE_BORROW = 2 }
  * LREP_FORM_KM: inputs are K and M directly. */
 enum { LREP_FORM_AB = 0, LREP_FORM_KM = 1 };
 enum { LREP_OP_K = 0, LREP_OP_M = 1 };
-/* Arithmetic of the operator products K X, M Y.
- * FP64: every product in float64.
- * MIXED_BF16X3: the inexact CG products of eq. block_GS use K, M split as
- *   hi + lo bfloat16 pairs (three bf16 tensor-core products, fp32
+/* Arithmetic of the operator products K X, M Y (dense operators only for
+ * anything but FP64; two independent bits).
+ * FP64: every product in float64 (FP64 FMA units).
+ * MIXED_BF16X3 (bit 0): the inexact CG products of eq. block_GS use K, M
+ *   split as hi + lo bfloat16 pairs (three bf16 tensor-core products, fp32
  *   accumulation); every product that enters H^ (eq. hat_H) and every
- *   residual (eq. tol) stays float64. */
-enum { LREP_PREC_FP64 = 0, LREP_PREC_MIXED_BF16X3 = 1 };
+ *   residual (eq. tol) keeps float64 accuracy.
+ * FP64_SLICED (bit 1): the float64-accurate products (and, without bit 0,
+ *   the CG products too) run on the bf16 tensor cores by error-free
+ *   slicing: K, M and each X held as seven base-2^8 digit planes under
+ *   power-of-two row / column scales, the 28 leading digit-pair products
+ *   summed exactly in integer arithmetic (levels 2..5) or in fp32 (levels
+ *   6..8, weight <= 2^-48).  Error <= ~2^-54.7 n 2^(e_i + f_j) per entry,
+ *   2^e_i and 2^f_j bounding row i of K (M) and column j of X: the form of
+ *   the float64 product's own bound.  Holds 14 bytes per matrix entry.
+ * MIXED_SLICED = both bits. */
+enum {
+  LREP_PREC_FP64 = 0,
+  LREP_PREC_MIXED_BF16X3 = 1,
+  LREP_PREC_FP64_SLICED = 2,
+  LREP_PREC_MIXED_SLICED = 3
+};
 
 typedef struct {
   int32_t struct_size;    /* sizeof(lrep_options), for versioning          */
@@ -137,6 +152,26 @@ lrep_status lrep_create_operator(lrep_problem* out, int64_t n,
 lrep_status lrep_set_nullspace(lrep_problem p, int32_t r, const double* X0,
                                const double* Y0, int64_t ld, int32_t mem);
 
+/* Pre-step for singular K (Remark on the numerical computation of the
+ * generalized nullspace): computes an orthonormal basis X0 of N(K) on the
+ * GPU by block LOBPCG on K (r_max + 4 columns, the problem's float64
+ * operator products) and installs it as by lrep_set_nullspace(p, r, X0,
+ * NULL, ...), so Y0 = M^-1 X0 follows by CG in the solve.  A Ritz pair
+ * counts as a null vector when its Ritz value is <= sqrt(tol) ||K||_2 and
+ * its residual <= tol ||K||_2 (||K||_2 by power steps); the search stops
+ * once every such pair has converged and the next Ritz value is certainly
+ * above sqrt(tol) ||K||_2.  0 <= r_max <= 60.  *r_host: dimension found
+ * (0: K nonsingular), *iters_host: LOBPCG iterations (may be NULL).  When
+ * X0_out is not NULL the basis is also copied there (n x r, leading
+ * dimension ld_out >= n, host memory for mem_out = LREP_MEM_HOST, device
+ * memory for LREP_MEM_DEVICE_COPY; room for r_max columns).
+ * LREP_NOT_CONVERGED after maxit iterations (no basis installed);
+ * LREP_ERR_ARG when the nullity exceeds r_max or K = 0. */
+lrep_status lrep_find_nullspace(lrep_problem p, int32_t r_max, double tol,
+                                int32_t maxit, double* X0_out, int64_t ld_out,
+                                int32_t mem_out, int32_t* r_host,
+                                int32_t* iters_host);
+
 lrep_status lrep_set_options(lrep_problem p, const lrep_options* opts);
 
 /* Optional start blocks U0, V0 (n x ncols, ncols >= s*nb + 2*nb for the
@@ -168,11 +203,13 @@ enum {
   LREP_Q_BIORTH_ERR = 10,/* float64: max |X^T Y - I| of the result          */
   LREP_Q_HISTORY = 11,   /* float64[iters]: max residual per iteration      */
   LREP_Q_REBIORTHS = 12, /* int32: safeguard re-biorthogonalisations        */
-  LREP_Q_PROFILE = 13    /* float64[4] with options.profile set: operator
+  LREP_Q_PROFILE = 13,   /* float64[4] with options.profile set: operator
                             product device time (s), product launches,
                             product flops (2 nnz per column), and product
                             algorithmic bytes (operator read once per
                             launch + input and output blocks)             */
+  LREP_Q_PROFILE_CG = 14 /* float64[4]: the same for the products of the CG
+                            operator alone (eq. block_GS)                 */
 };
 lrep_status lrep_query(lrep_problem p, int32_t what, void* dst,
                        int64_t dst_bytes, int32_t mem);

@@ -55,6 +55,10 @@ lrep_status apply_op(lrep_problem p, int which, int c, const double* X,
   const bool isK = (which == LREP_OP_K);
   switch (o.kind) {
     case OP_DENSE:
+      if (p->opts.precision & LREP_PREC_FP64_SLICED) {
+        if (!o.ozK) return p->fail(LREP_ERR_STATE, "digit planes of the operator missing");
+        return apply_sliced(p, which, c, X, ldx, Y, ldy, skip, ws, ws_elems);
+      }
       e = dense_apply_f64(o.n, c, isK ? o.K : o.M, o.ld, X, ldx, Y, ldy, ws,
                           ws_elems, skip, p->stream);
       break;
@@ -324,7 +328,13 @@ struct Solver {
     double nnz = 0.0, opbytes = 0.0;
     if (o.kind == OP_DENSE) {
       nnz = (double)n * n;
-      opbytes = (cgop && p->opts.precision == LREP_PREC_MIXED_BF16X3) ? 4.0 * nnz : 8.0 * nnz;
+      const int prec = p->opts.precision;
+      if (cgop && (prec & LREP_PREC_MIXED_BF16X3))
+        opbytes = 4.0 * nnz;   // hi + lo bf16
+      else if (prec & LREP_PREC_FP64_SLICED)
+        opbytes = 14.0 * nnz;  // 7 bf16 digit planes
+      else
+        opbytes = 8.0 * nnz;
     } else if (o.kind == OP_STENCIL) {
       nnz = 7.0 * n;
       opbytes = 8.0 * n;  // the diagonal
@@ -332,10 +342,11 @@ struct Solver {
       nnz = 7.0 * n;
       opbytes = 12.0 * nnz + 8.0 * (n + 1);
     }
-    p->prof[0] += ms * 1e-3;
-    p->prof[1] += 1.0;
-    p->prof[2] += 2.0 * nnz * c;
-    p->prof[3] += opbytes + 16.0 * n * c;
+    const double add[4] = {ms * 1e-3, 1.0, 2.0 * nnz * c, opbytes + 16.0 * n * c};
+    for (int i = 0; i < 4; ++i) {
+      p->prof[i] += add[i];
+      if (cgop) p->prof_cg[i] += add[i];
+    }
   }
 
   // Block CG (one CG per column) for op * X = B; check_every > 0 reads the
@@ -801,6 +812,7 @@ lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol, SmallBatcher
   configure(S, p, nev, nb, tol);
   S.batcher = batcher;
   for (double& v : p->prof) v = 0.0;
+  for (double& v : p->prof_cg) v = 0.0;
   if (S.dmax > 256) return p->fail(LREP_ERR_ARG, "window + 2*block exceeds 256 columns");
   if (S.nb > 64) return p->fail(LREP_ERR_ARG, "block exceeds 64");
   if ((int64_t)S.dmax > S.n - S.r) return p->fail(LREP_ERR_ARG, "n too small for nev/block");

@@ -287,21 +287,45 @@ lrep_status lrep_set_nullspace(lrep_problem p, int32_t r, const double* X0,
   return LREP_OK;
 }
 
+lrep_status lrep_find_nullspace(lrep_problem p, int32_t r_max, double tol, int32_t maxit,
+                                double* X0_out, int64_t ld_out, int32_t mem_out,
+                                int32_t* r_host, int32_t* iters_host) {
+  if (!p) return LREP_ERR_ARG;
+  if (r_max < 0 || r_max > 60 || !(tol > 0.0) || !(tol < 1.0) || maxit < 1 || !r_host ||
+      (X0_out && (ld_out < p->op.n ||
+                  (mem_out != LREP_MEM_HOST && mem_out != LREP_MEM_DEVICE_COPY))))
+    return p->fail(LREP_ERR_ARG, "lrep_find_nullspace: invalid argument (0 <= r_max <= 60)");
+  int r = 0, its = 0;
+  const lrep_status s = find_nullspace(p, r_max, tol, maxit, &r, &its);
+  if (s != LREP_OK) return s;
+  if (X0_out && r > 0) {
+    PCK(p, cudaMemcpy2DAsync(X0_out, ld_out * sizeof(double), p->X0in,
+                             pad_ld(p->op.n) * sizeof(double), p->op.n * sizeof(double), r,
+                             mem_out == LREP_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                      : cudaMemcpyDeviceToDevice,
+                             p->stream));
+    PCK(p, cudaStreamSynchronize(p->stream));
+  }
+  *r_host = r;
+  if (iters_host) *iters_host = its;
+  return LREP_OK;
+}
+
 lrep_status lrep_set_options(lrep_problem p, const lrep_options* o) {
   if (!p || !o) return LREP_ERR_ARG;
   if (o->struct_size != (int32_t)sizeof(lrep_options))
     return p->fail(LREP_ERR_ARG, "lrep_set_options: struct_size mismatch");
   if (o->s < 2 || o->ngs < 1 || o->cg_maxit < 0 || !(o->cg_tol > 0.0) || o->maxit < 1 ||
       !(o->discard_tol >= 0.0) || o->refresh_every < 1 || !(o->rebiorth_tol > 0.0) ||
-      (o->precision != LREP_PREC_FP64 && o->precision != LREP_PREC_MIXED_BF16X3))
+      o->precision < LREP_PREC_FP64 || o->precision > LREP_PREC_MIXED_SLICED)
     return p->fail(LREP_ERR_ARG, "lrep_set_options: invalid value");
-  if (o->precision == LREP_PREC_MIXED_BF16X3 && p->op.kind != OP_DENSE)
-    return p->fail(LREP_ERR_ARG, "mixed precision needs a dense operator");
+  if (o->precision != LREP_PREC_FP64 && p->op.kind != OP_DENSE)
+    return p->fail(LREP_ERR_ARG, "tensor-core precisions need a dense operator");
   const bool rebuild = (o->precision != p->opts.precision);
   p->opts = *o;
   if (rebuild) {
     free_split(p);
-    if (o->precision == LREP_PREC_MIXED_BF16X3) return build_split(p);
+    if (o->precision != LREP_PREC_FP64) return build_split(p);
   }
   return LREP_OK;
 }
@@ -388,6 +412,7 @@ lrep_status lrep_query(lrep_problem p, int32_t what, void* dst, int64_t dst_byte
       return put(p->history.data(), sizeof(double) * (int64_t)p->history.size(), false);
     case LREP_Q_REBIORTHS: { int32_t v = p->rebiorths; return put(&v, sizeof(v), false); }
     case LREP_Q_PROFILE: return put(p->prof, sizeof(p->prof), false);
+    case LREP_Q_PROFILE_CG: return put(p->prof_cg, sizeof(p->prof_cg), false);
     default: return p->fail(LREP_ERR_ARG, "lrep_query: unknown item");
   }
 }

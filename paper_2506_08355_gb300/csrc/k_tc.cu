@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "tc.h"
+#include "tcgen05.cuh"
 
 namespace lrep {
 namespace {
@@ -31,74 +32,8 @@ constexpr int BM = 128;              // output rows per CTA = TMEM lanes
 constexpr int BK = 64;               // k per stage: 64 bf16 = 128 B (one swizzle row)
 constexpr int STAGES = 4;
 constexpr int TILE_A = BM * BK * 2;  // 16 KB
-constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait; returns false (and records `code`) when the limit expires
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err, int code) {
-  const long long t0 = clock64();
-  while (!mbar_try(a, parity)) {
-    if (clock64() - t0 > WAIT_CYCLES) {
-      atomicExch(err, code);
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t mbar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y)
-      : "memory");
-}
-
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), descriptor version 1
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;               // LBO (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;     // SBO
-  d |= (uint64_t)1 << 46;               // version
-  d |= (uint64_t)2 << 61;               // SWIZZLE_128B
-  return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   mbar)
-               : "memory");
-}
+using namespace tc5;
 
 __global__ void __launch_bounds__(128, 1)
 bf16x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,

@@ -1,48 +1,93 @@
-// Mixed-precision CG operator (LREP_PREC_MIXED_BF16X3): K and M split once
-// into bfloat16 hi + lo parts; the CG products of eq. block_GS run on the
-// tensor cores (k_tc.cu).  Every product that enters H^ (eq. hat_H) and
-// every residual (eq. tol) stays float64.
+// Tensor-core operators of the dense K and M, built once per problem from
+// the float64 matrices according to opts.precision:
+//  * bit 0 (MIXED_BF16X3): hi + lo bfloat16 split for the inexact CG
+//    products of eq. block_GS (k_tc.cu);
+//  * bit 1 (FP64_SLICED): seven bf16 digit planes for float64-accurate
+//    products by error-free slicing (k_oz.cu): every product that enters H^
+//    (eq. hat_H) and every residual (eq. tol), and the CG products when bit 0
+//    is clear.
+// Without bit 1, float64 products use the FP64 kernels.
 #include <cuda_runtime.h>
 
+#include "oz.h"
 #include "problem.h"
 #include "tc.h"
 
 namespace lrep {
 
+namespace {
+bool want_tc(const lrep_problem p) { return (p->opts.precision & LREP_PREC_MIXED_BF16X3) != 0; }
+bool want_oz(const lrep_problem p) { return (p->opts.precision & LREP_PREC_FP64_SLICED) != 0; }
+}  // namespace
+
+bool split_ready(lrep_problem p) {
+  const Operator& o = p->op;
+  return (!want_tc(p) || o.tcK) && (!want_oz(p) || o.ozK);
+}
+
+size_t split_bytes(lrep_problem p) {
+  const int64_t n = p->op.n;
+  size_t b = 0;
+  if (want_tc(p)) b += (size_t)2 * 2 * 2 * tc_ld(n) * n;  // K, M x (hi, lo) bf16
+  if (want_oz(p)) b += (size_t)2 * oz_operand_bytes(n);   // K, M x 7 digit planes
+  return b;
+}
+
 lrep_status build_split(lrep_problem p) {
   Operator& o = p->op;
-  if (o.kind != OP_DENSE) return p->fail(LREP_ERR_ARG, "mixed precision needs a dense operator");
   free_split(p);
-  const int64_t n = o.n, ldb = tc_ld(n);
-  const size_t bytes = (size_t)ldb * n * 2;
-  TcOperand* t[2] = {new TcOperand(), new TcOperand()};
-  o.tcK = t[0];
-  o.tcM = t[1];
+  if (p->opts.precision == LREP_PREC_FP64) return LREP_OK;
+  if (o.kind != OP_DENSE)
+    return p->fail(LREP_ERR_ARG, "tensor-core precisions need a dense operator");
+  const int64_t n = o.n;
   const double* src[2] = {o.K, o.M};
-  for (int i = 0; i < 2; ++i) {
-    cudaError_t e = cudaMalloc(&t[i]->hi, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&t[i]->lo, bytes);
-    if (e != cudaSuccess) {
-      free_split(p);
-      return p->fail(LREP_ERR_NOMEM, "bf16 split of the operator: out of device memory");
+  if (want_tc(p)) {
+    const int64_t ldb = tc_ld(n);
+    const size_t bytes = (size_t)ldb * n * 2;
+    TcOperand* t[2] = {new TcOperand(), new TcOperand()};
+    o.tcK = t[0];
+    o.tcM = t[1];
+    for (int i = 0; i < 2; ++i) {
+      cudaError_t e = cudaMalloc(&t[i]->hi, bytes);
+      if (e == cudaSuccess) e = cudaMalloc(&t[i]->lo, bytes);
+      if (e != cudaSuccess) {
+        free_split(p);
+        return p->fail(LREP_ERR_NOMEM, "bf16 split of the operator: out of device memory");
+      }
+      t[i]->ldb = ldb;
+      e = tc_split_matrix(n, n, src[i], o.ld, t[i]->hi, t[i]->lo, ldb, p->stream);
+      if (e != cudaSuccess) {
+        free_split(p);
+        return p->fail(LREP_ERR_CUDA, std::string("bf16 split: ") + cudaGetErrorString(e));
+      }
+      if (!tc_make_map(&t[i]->hi_map, t[i]->hi, n, n, ldb, 64, 128) ||
+          !tc_make_map(&t[i]->lo_map, t[i]->lo, n, n, ldb, 64, 128)) {
+        free_split(p);
+        return p->fail(LREP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the operator split");
+      }
     }
-    t[i]->ldb = ldb;
-    e = tc_split_matrix(n, n, src[i], o.ld, t[i]->hi, t[i]->lo, ldb, p->stream);
-    if (e != cudaSuccess) {
-      free_split(p);
-      return p->fail(LREP_ERR_CUDA, std::string("bf16 split: ") + cudaGetErrorString(e));
-    }
-    if (!tc_make_map(&t[i]->hi_map, t[i]->hi, n, n, ldb, 64, 128) ||
-        !tc_make_map(&t[i]->lo_map, t[i]->lo, n, n, ldb, 64, 128)) {
-      free_split(p);
-      return p->fail(LREP_ERR_CUDA, "cuTensorMapEncodeTiled failed for the operator split");
+  }
+  if (want_oz(p)) {
+    OzOperand* z[2] = {new OzOperand(), new OzOperand()};
+    o.ozK = z[0];
+    o.ozM = z[1];
+    for (int i = 0; i < 2; ++i) {
+      if (cudaMalloc(&z[i]->slices, oz_operand_bytes(n)) != cudaSuccess) {
+        free_split(p);
+        return p->fail(LREP_ERR_NOMEM, "digit planes of the operator: out of device memory");
+      }
+      const cudaError_t e = oz_slice_operator(n, src[i], o.ld, z[i], p->stream);
+      if (e != cudaSuccess) {
+        free_split(p);
+        return p->fail(LREP_ERR_CUDA, std::string("digit planes: ") + cudaGetErrorString(e));
+      }
     }
   }
   if (cudaMalloc(&o.tc_err, sizeof(int)) != cudaSuccess ||
       cudaMemsetAsync(o.tc_err, 0, sizeof(int), p->stream) != cudaSuccess ||
       cudaStreamSynchronize(p->stream) != cudaSuccess) {
     free_split(p);
-    return p->fail(LREP_ERR_CUDA, "bf16 split: device error");
+    return p->fail(LREP_ERR_CUDA, "tensor-core operator: device error");
   }
   return LREP_OK;
 }
@@ -57,21 +102,38 @@ void free_split(lrep_problem p) {
       *t = nullptr;
     }
   }
+  for (OzOperand** z : {&o.ozK, &o.ozM}) {
+    if (*z) {
+      if ((*z)->slices) cudaFree((*z)->slices);
+      delete *z;
+      *z = nullptr;
+    }
+  }
   if (o.tc_err) cudaFree(o.tc_err);
   o.tc_err = nullptr;
 }
 
 size_t apply_cg_ws_elems(lrep_problem p, int c) {
-  if (p->opts.precision == LREP_PREC_MIXED_BF16X3 && p->op.tcK)
-    return tc_ws_bytes(p->op.n, c) / sizeof(double) + 1;
-  return 0;
+  size_t b = 0;
+  if (p->op.tcK) b = std::max(b, tc_ws_bytes(p->op.n, c));
+  if (p->op.ozK) b = std::max(b, oz_ws_bytes(p->op.n, c));
+  return b ? b / sizeof(double) + 1 : 0;
+}
+
+lrep_status apply_sliced(lrep_problem p, int which, int c, const double* X, int64_t ldx,
+                         double* Y, int64_t ldy, const int* skip, double* ws, size_t ws_elems) {
+  const Operator& o = p->op;
+  cudaError_t e = oz_apply(which == LREP_OP_K ? *o.ozK : *o.ozM, c, X, ldx, Y, ldy, ws,
+                           ws_elems * sizeof(double), o.tc_err, skip, p->stream);
+  if (e != cudaSuccess)
+    return p->fail(LREP_ERR_CUDA, std::string("sliced product: ") + cudaGetErrorString(e));
+  return LREP_OK;
 }
 
 lrep_status apply_op_cg(lrep_problem p, int which, int c, const double* X,
                         int64_t ldx, double* Y, int64_t ldy, const int* skip,
                         double* ws, size_t ws_elems) {
-  if (p->opts.precision == LREP_PREC_FP64)
-    return apply_op(p, which, c, X, ldx, Y, ldy, skip, ws, ws_elems);
+  if (!want_tc(p)) return apply_op(p, which, c, X, ldx, Y, ldy, skip, ws, ws_elems);
   const Operator& o = p->op;
   if (!o.tcK) return p->fail(LREP_ERR_STATE, "mixed precision operator split missing");
   cudaError_t e = tc_apply(which == LREP_OP_K ? *o.tcK : *o.tcM, o.n, c, X, ldx, Y, ldy, ws,

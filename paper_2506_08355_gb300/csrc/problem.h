@@ -12,6 +12,7 @@
 
 namespace lrep {
 struct TcOperand;
+struct OzOperand;
 
 enum OpKind { OP_DENSE = 0, OP_CSR = 1, OP_STENCIL = 2, OP_CALLBACK = 3 };
 
@@ -56,7 +57,10 @@ struct Operator {
   // mixed precision: bf16 hi/lo split of dense K and M (tc.h)
   struct TcOperand* tcK = nullptr;
   struct TcOperand* tcM = nullptr;
-  int* tc_err = nullptr;  // pipeline timeout flag of the tensor-core kernel
+  // sliced float64 emulation: 7 bf16 digit planes of dense K and M (oz.h)
+  struct OzOperand* ozK = nullptr;
+  struct OzOperand* ozM = nullptr;
+  int* tc_err = nullptr;  // pipeline timeout flag of the tensor-core kernels
   std::vector<void*> owned;  // device allocations freed at destroy
 };
 
@@ -94,6 +98,7 @@ struct lrep_problem_s {
   bool solved = false;
   // operator-product profile (options.profile)
   double prof[4] = {0, 0, 0, 0};
+  double prof_cg[4] = {0, 0, 0, 0};  // CG-operator products alone
   // scratch for op-level calls on this problem
   lrep::Arena op_arena;
   // solver workspace (kept between solves of the same shape)
@@ -115,6 +120,10 @@ lrep_status apply_op(lrep_problem p, int which, int c, const double* X,
 lrep_status apply_op_cg(lrep_problem p, int which, int c, const double* X,
                         int64_t ldx, double* Y, int64_t ldy, const int* skip,
                         double* ws, size_t ws_elems);
+// y = op(X) by the sliced float64 emulation (dense, digit planes built)
+lrep_status apply_sliced(lrep_problem p, int which, int c, const double* X,
+                         int64_t ldx, double* Y, int64_t ldy, const int* skip,
+                         double* ws, size_t ws_elems);
 size_t apply_ws_elems(lrep_problem p, int c);
 size_t apply_cg_ws_elems(lrep_problem p, int c);
 // Cross-solve batching of the small projected problems (serving): when
@@ -128,7 +137,14 @@ lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol,
                        SmallBatcher* batcher = nullptr);
 // device bytes the solver's workspace needs for (nev, nb) on p
 size_t bosp_footprint(lrep_problem p, int nev, int nb);
-// mixed precision: build the bf16 hi/lo split of the dense operator
+// orthonormal basis of N(K) by LOBPCG (nullspace.cu); sets p->r, p->X0in
+lrep_status find_nullspace(lrep_problem p, int r_max, double tol, int maxit, int* r_out,
+                           int* iters_out);
+// tensor-core precisions: build what opts.precision needs of the bf16 hi/lo
+// split and the digit planes of the dense operator
 lrep_status build_split(lrep_problem p);
 void free_split(lrep_problem p);
+bool split_ready(lrep_problem p);
+// device bytes build_split allocates for opts.precision
+size_t split_bytes(lrep_problem p);
 }  // namespace lrep

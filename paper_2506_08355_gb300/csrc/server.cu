@@ -167,9 +167,11 @@ struct lrep_server_s {
         idle++;
         cv_work.notify_all();
         cv_work.wait(g, [&] { return stop || admissible(); });
+        // decide while this worker still counts as idle
+        const bool take = admissible();
         idle--;
         if (stop && queue.empty()) break;
-        if (!admissible()) continue;
+        if (!take) continue;
         r = queue.front();
         queue.pop_front();
         in_use += (int64_t)r.footprint;
@@ -179,8 +181,7 @@ struct lrep_server_s {
       cudaStream_t own = r.p->stream;
       r.p->stream = st;
       lrep_status s = LREP_OK;
-      if (r.p->opts.precision == LREP_PREC_MIXED_BF16X3 && !r.p->op.tcK)
-        s = build_split(r.p);
+      if (!split_ready(r.p)) s = build_split(r.p);
       if (s == LREP_OK) {
         r.p->err.clear();
         s = bosp_solve(r.p, r.nev, r.block, r.tol, &batcher);
@@ -226,8 +227,7 @@ lrep_status lrep_server_create(lrep_server* out, int64_t hbm_budget_bytes, int32
 lrep_status lrep_footprint(lrep_problem p, int32_t nev, int32_t block, int64_t* bytes) {
   if (!p || !bytes || nev < 1 || block < 1) return LREP_ERR_ARG;
   size_t fp = bosp_footprint(p, nev, block);
-  if (p->opts.precision == LREP_PREC_MIXED_BF16X3 && !p->op.tcK)
-    fp += (size_t)2 * 2 * 2 * ((p->op.n + 63) / 64 * 64) * p->op.n;  // K, M x (hi, lo) bf16
+  if (!split_ready(p)) fp += split_bytes(p);
   *bytes = (int64_t)fp;
   return LREP_OK;
 }

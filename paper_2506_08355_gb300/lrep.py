@@ -22,9 +22,9 @@ ERR = {-1: "ERR_ARG", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_NOT_SPD",
 MEM_HOST, MEM_DEVICE_COPY, MEM_DEVICE_BORROW = 0, 1, 2
 FORM_AB, FORM_KM = 0, 1
 OP_K, OP_M = 0, 1
-PREC_FP64, PREC_MIXED_BF16X3 = 0, 1
+PREC_FP64, PREC_MIXED_BF16X3, PREC_FP64_SLICED, PREC_MIXED_SLICED = 0, 1, 2, 3
 (Q_NCONV, Q_EIGVALS, Q_X, Q_Y, Q_U, Q_V, Q_RESID, Q_ITERS, Q_MATVECS, Q_TIMINGS,
- Q_BIORTH_ERR, Q_HISTORY, Q_REBIORTHS, Q_PROFILE) = range(14)
+ Q_BIORTH_ERR, Q_HISTORY, Q_REBIORTHS, Q_PROFILE, Q_PROFILE_CG) = range(15)
 
 
 class Options(C.Structure):
@@ -54,6 +54,9 @@ EXPORTS = {
                                        C.c_void_p, C.c_void_p]),
     "lrep_set_nullspace": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                      C.c_int64, C.c_int32]),
+    "lrep_find_nullspace": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32,
+                                      C.c_void_p, C.c_int64, C.c_int32,
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lrep_set_options": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
     "lrep_set_start": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.c_int64, C.c_int32]),
@@ -267,6 +270,15 @@ class Problem:
             y, _, _ = block_arg(Y0, self.n)
         _check(lib().lrep_set_nullspace(self.h, r, _ptr(x), _ptr(y), ldx, mem), self.h)
 
+    def find_nullspace(self, r_max=8, tol=1e-10, maxit=2000):
+        """Basis of N(K) by LOBPCG on the GPU, installed as the nullspace;
+        returns (X0 as an n x r numpy array, iterations)."""
+        r, it = C.c_int32(), C.c_int32()
+        out = np.zeros((max(r_max, 1), self.n), dtype=np.float64)
+        _check(lib().lrep_find_nullspace(self.h, r_max, tol, maxit, _ptr(out), self.n, MEM_HOST,
+                                         C.byref(r), C.byref(it)), self.h)
+        return out[: r.value].T.copy(), it.value
+
     def set_options(self, **kw):
         o = default_options(**kw)
         _check(lib().lrep_set_options(self.h, C.byref(o)), self.h)
@@ -341,6 +353,10 @@ class Problem:
     def profile(self):
         """(product seconds, product launches, flops, algorithmic bytes)."""
         return self._q_array(Q_PROFILE, 4)
+
+    def profile_cg(self):
+        """profile() restricted to the CG-operator products."""
+        return self._q_array(Q_PROFILE_CG, 4)
 
     # op level --------------------------------------------------------------
     def apply(self, op, X, Y, cg=False):
