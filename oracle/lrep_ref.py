@@ -161,6 +161,27 @@ def lrep_definition(K, M, nev, r=0, FK=None, FM=None):
     return sig, X, Y
 
 
+def lrep_definition_gen(K, M, Bm, nev, r=0):
+    """Generalized LREP (Remark on the generalized LREP): K x = lam B y,
+    M y = lam B x with B symmetric positive definite, x^T B y = 1.
+
+    With B = L L^T: K' = L^-1 K L^-T, M' = L^-1 M L^-T is a standard LREP
+    with x' = L^T x, y' = L^T y (K' x' = L^-1 K x = lam L^-1 B y = lam y',
+    and x'^T y' = x^T B y), solved by ``lrep_definition``.
+    Returns (lam ascending, X, Y) with X, Y of shape n x nev.
+    """
+    L = np.linalg.cholesky(np.asarray(Bm, dtype=np.float64))
+    Kp = np.linalg.solve(L, np.linalg.solve(L, np.asarray(K, dtype=np.float64)).T)
+    Mp = np.linalg.solve(L, np.linalg.solve(L, np.asarray(M, dtype=np.float64)).T)
+    Kp = 0.5 * (Kp + Kp.T)
+    Mp = 0.5 * (Mp + Mp.T)
+    lam, Xp, Yp = lrep_definition(Kp, Mp, nev, r)
+    X = np.linalg.solve(L.T, Xp)
+    Y = np.linalg.solve(L.T, Yp)
+    X, Y = fix_sign(X, Y)
+    return lam, X, Y
+
+
 def lrep_definition_values(FK, FM, nev, r=0):
     """Eigenvalues only of the definition route (one values-only SVD of
     F_K^T F_M), for orders where the vectors are not needed.

@@ -428,3 +428,33 @@ def test_nullspace_definition_recovers_chosen_kernel():
     assert X1.shape == (n, 0)
     X2, _ = R.nullspace_definition(np.zeros((5, 5)), 1e-10)
     assert X2.shape == (5, 5)
+
+
+def test_generalized_definition_pins():
+    """Remark on the generalized LREP: (i) B = beta I scales the spectrum by
+    1/beta and the vectors by beta^-1/2; (ii) the positive eigenvalues of
+    the pencil ([[0, K], [M, 0]], diag(B, B)) by a general eigensolver;
+    (iii) K X = B Y Lam, M Y = B X Lam, X^T B Y = I."""
+    import scipy.linalg as sla
+    rng = np.random.default_rng(21)
+    n, nev = 14, 5
+    Q1, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    K = (Q1 * rng.uniform(0.5, 10, n)) @ Q1.T
+    M = (Q2 * rng.uniform(0.5, 10, n)) @ Q2.T
+    lam, X, Y = R.lrep_definition(K, M, nev)
+    beta = 2.5
+    lb, Xb, Yb = R.lrep_definition_gen(K, M, beta * np.eye(n), nev)
+    np.testing.assert_allclose(lb, lam / beta, rtol=1e-12)
+    np.testing.assert_allclose(Xb, X / np.sqrt(beta), atol=1e-10)
+    A = rng.standard_normal((n, n))
+    Bm = A @ A.T + n * np.eye(n)
+    lg, Xg, Yg = R.lrep_definition_gen(K, M, Bm, nev)
+    H = np.block([[np.zeros((n, n)), K], [M, np.zeros((n, n))]])
+    Bb = np.block([[Bm, np.zeros((n, n))], [np.zeros((n, n)), Bm]])
+    ev = sla.eigvals(H, Bb)
+    pos = np.sort(ev.real[ev.real > 0])[:nev]
+    np.testing.assert_allclose(lg, pos, rtol=1e-9)
+    np.testing.assert_allclose(K @ Xg, Bm @ Yg * lg, atol=1e-9)
+    np.testing.assert_allclose(M @ Yg, Bm @ Xg * lg, atol=1e-9)
+    np.testing.assert_allclose(Xg.T @ Bm @ Yg, np.eye(nev), atol=1e-10)
