@@ -391,10 +391,16 @@ def serve_mode(args):
     sub = {i: ts for (i, t, ts) in tickets}
     lat = np.array([done_at[i] - sub[i] for i in range(len(probs))]) * 1e3
     ok = sum(1 for v in status.values() if v == 0)
-    total_nev = sum(p[1] for p in probs)
+    failed = {}
+    for i, v in status.items():
+        if v != 0 and len(failed) < 5:
+            failed[i] = {"status": int(v), "n": probs[i][2], "nev": probs[i][1],
+                         "error": lrep.lib().lrep_last_error(probs[i][0].h).decode()}
+    total_nev = sum(p[1] for i, p in enumerate(probs) if status[i] == 0)
     worst = 0.0
-    for pr, nev, n, ta in probs[:: max(1, len(probs) // 50)]:
-        worst = max(worst, float(pr.residuals().max()))
+    for i in range(0, len(probs), max(1, len(probs) // 50)):
+        if status[i] == 0:
+            worst = max(worst, float(probs[i][0].residuals().max()))
     stats = srv.stats()
     srv.close()
     for pr, *_ in probs:
@@ -403,7 +409,8 @@ def serve_mode(args):
             "value": total_nev / makespan, "unit": "eigenpairs/s", "n_gpus": 1,
             "higher_is_better": True, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "requests": len(probs), "ok": ok, "makespan_s": makespan,
+            "requests": len(probs), "ok": ok, "failed_examples": failed,
+            "makespan_s": makespan,
             "sampled_max_residual": worst, "slots": args.slots,
             "shared_small_lrep_launches": {"batches": stats[0], "problems": stats[1],
                                            "largest": stats[2]},

@@ -22,7 +22,7 @@
 
 namespace lrep {
 
-cudaError_t Arena::reserve(size_t bytes) {
+cudaError_t Arena::reserve(size_t bytes, cudaStream_t st) {
   release();
   if (bytes == 0) bytes = 256;
   cudaError_t e = cudaMalloc(&base, bytes);
@@ -32,7 +32,9 @@ cudaError_t Arena::reserve(size_t bytes) {
   }
   cap = bytes;
   off = 0;
-  return cudaMemset(base, 0, bytes);
+  // zero-filled in the order of the stream that will use it (a legacy-stream
+  // memset would not be ordered before work on a non-blocking stream)
+  return cudaMemsetAsync(base, 0, bytes, st);
 }
 
 void Arena::release() {
@@ -148,6 +150,7 @@ struct Solver {
     int tc_err;
     int act[64];
     double lam_act[64];
+    int pflag[520];  // profile: skip flag seen by each pending CG product
   }* h = nullptr;
   // host control state
   int ell = 0, w_prev = 0;
@@ -160,6 +163,7 @@ struct Solver {
     cudaEvent_t a, b;
     int c;
     bool cgop;
+    int flag;  // index into h->pflag, or -1 (product always runs)
   };
   std::vector<cudaEvent_t> prof_free, prof_all;
   std::vector<Pending> prof_pending;
@@ -181,7 +185,7 @@ struct Solver {
     for (const Pending& q : prof_pending) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, q.a, q.b);
-      account_product(q.c, ms, q.cgop);
+      if (q.flag < 0 || h->pflag[q.flag] == 0) account_product(q.c, ms, q.cgop);
       prof_free.push_back(q.a);
       prof_free.push_back(q.b);
     }
@@ -267,7 +271,7 @@ struct Solver {
     bool reuse = (A.base != nullptr) && A.cap >= bytes;
     for (int i = 0; i < 4; ++i) reuse = reuse && p->ws_key[i] == key[i];
     if (!reuse) {
-      LCK(A.reserve(bytes));
+      LCK(A.reserve(bytes, st));
       for (int i = 0; i < 4; ++i) p->ws_key[i] = key[i];
     } else {
       LCK(cudaMemsetAsync(A.base, 0, A.cap, st));
@@ -305,7 +309,7 @@ struct Solver {
                     const int* skip = nullptr, bool cgop = false) {
     if (c <= 0) return LREP_OK;
     p->matvecs += skip ? 0 : c;
-    const bool prof = p->opts.profile && !skip;
+    const bool prof = p->opts.profile != 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (prof) {
       LST(take_event(&e0));
@@ -316,8 +320,13 @@ struct Solver {
                          : apply_op(p, which, c, X, ld, Y, ld, skip, ws, ws_elems);
     if (prof && s == LREP_OK) {
       LCK(cudaEventRecord(e1, st));
-      prof_pending.push_back(Pending{e0, e1, c, cgop});
-      if (prof_pending.size() > 512) LST(sync());
+      int flag = -1;
+      if (skip) {  // products skipped on the device (converged CG) are not counted
+        flag = (int)prof_pending.size();
+        LCK(cudaMemcpyAsync(&h->pflag[flag], skip, sizeof(int), cudaMemcpyDeviceToHost, st));
+      }
+      prof_pending.push_back(Pending{e0, e1, c, cgop, flag});
+      if (prof_pending.size() >= 512) LST(sync());
     }
     return s;
   }

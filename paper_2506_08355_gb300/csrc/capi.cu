@@ -87,7 +87,7 @@ struct Pool {
 };
 Pool g_pool;
 
-lrep_status pool_take(size_t elems, double** out) {
+lrep_status pool_take(size_t elems, double** out, void* stream) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 16) return cuda_fail(nullptr, "cudaGetDevice", e);
@@ -95,7 +95,7 @@ lrep_status pool_take(size_t elems, double** out) {
   Arena& A = g_pool.arena[dev];
   const size_t bytes = (elems + 64) * sizeof(double);
   if (A.cap < bytes) {
-    e = A.reserve(std::max(bytes, (size_t)1 << 20));
+    e = A.reserve(std::max(bytes, (size_t)1 << 20), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, "scratch pool", e);
   }
   *out = reinterpret_cast<double*>(A.base);
@@ -444,7 +444,7 @@ lrep_status lrep_op_apply(lrep_problem p, int32_t op, int32_t ncols, const doubl
     return p ? p->fail(LREP_ERR_ARG, "lrep_op_apply: invalid argument") : LREP_ERR_ARG;
   const size_t ws = apply_ws_elems(p, ncols);
   if (p->op_arena.cap < (ws + 64) * sizeof(double))
-    PCK(p, p->op_arena.reserve((ws + 64) * sizeof(double)));
+    PCK(p, p->op_arena.reserve((ws + 64) * sizeof(double), p->stream));
   return apply_op(p, op, ncols, X, ldx, Y, ldy, nullptr,
                   reinterpret_cast<double*>(p->op_arena.base), ws);
 }
@@ -456,7 +456,7 @@ lrep_status lrep_op_apply_cg(lrep_problem p, int32_t op, int32_t ncols, const do
     return p ? p->fail(LREP_ERR_ARG, "lrep_op_apply_cg: invalid argument") : LREP_ERR_ARG;
   const size_t ws = apply_ws_elems(p, ncols);
   if (p->op_arena.cap < (ws + 64) * sizeof(double))
-    PCK(p, p->op_arena.reserve((ws + 64) * sizeof(double)));
+    PCK(p, p->op_arena.reserve((ws + 64) * sizeof(double), p->stream));
   lrep_status s = apply_op_cg(p, op, ncols, X, ldx, Y, ldy, nullptr,
                               reinterpret_cast<double*>(p->op_arena.base), ws);
   if (s == LREP_OK && p->op.tc_err) {
@@ -479,7 +479,7 @@ lrep_status lrep_op_gram(int64_t n, int32_t a, int32_t b, const double* A, int64
   if (a == 0 || b == 0) return LREP_OK;
   const size_t need = gram_ws_elems(n, a, b);
   double* ws = nullptr;
-  lrep_status s = pool_take(need, &ws);
+  lrep_status s = pool_take(need, &ws, stream);
   if (s != LREP_OK) return s;
   if (n == 0) {
     cudaError_t e = cudaMemset2DAsync(G, ldg * sizeof(double), 0, a * sizeof(double), b,
@@ -512,7 +512,7 @@ lrep_status lrep_op_small_lrep(int32_t d, const double* Khat, const double* Mhat
     return LREP_ERR_ARG;
   }
   double* ws = nullptr;
-  lrep_status s = pool_take(small_work_elems(d) + 8, &ws);
+  lrep_status s = pool_take(small_work_elems(d) + 8, &ws, stream);
   if (s != LREP_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   SmallJob J{};
@@ -541,7 +541,7 @@ lrep_status lrep_op_biorth(int64_t n, int32_t m, const double* W, const double* 
   const size_t need = gram_ws_elems(n, 2 * m, 2 * m) + g + 4 * (size_t)m * m +
                       biorth_coef_work_elems(m) + 2 * (size_t)ld * m + 64;
   double* ws = nullptr;
-  lrep_status s = pool_take(need, &ws);
+  lrep_status s = pool_take(need, &ws, stream);
   if (s != LREP_OK) return s;
   double* G2 = ws;
   double* cA = G2 + g;
@@ -592,7 +592,7 @@ lrep_status lrep_op_residuals(int64_t n, int32_t w, const double* X, const doubl
   if (w == 0) return LREP_OK;
   const size_t need = residual_ws_elems(n, w) + 64;
   double* ws = nullptr;
-  lrep_status s = pool_take(need, &ws);
+  lrep_status s = pool_take(need, &ws, stream);
   if (s != LREP_OK) return s;
   unsigned int* counter = reinterpret_cast<unsigned int*>(ws);
   cudaStream_t st = (cudaStream_t)stream;

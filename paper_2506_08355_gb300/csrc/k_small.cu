@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -106,6 +108,22 @@ __device__ void mm_d(int d, const double* A, bool transA, const double* B, doubl
   __syncthreads();
 }
 
+// Jacobi rotation tangent t of the 2 x 2 problem [[aa, g], [g, bb]] (the
+// one-sided Jacobi angle of two columns with squared norms aa, bb and inner
+// product g); 0 when g = 0.
+__device__ __forceinline__ double pair_rotation(double aa, double bb, double g) {
+  if (g == 0.0) return 0.0;
+  const double zeta = (bb - aa) / (2.0 * g);
+  return (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+}
+
+// Simultaneous first-order rotations (V <- V (I + T - T^T)) are applied only
+// where |t| <= kRotCap; larger rotations (relative gap of the pair's singular
+// values below ~cos / kRotCap, e.g. a degenerate cluster) are done exactly,
+// one pair at a time, after the simultaneous steps.
+constexpr double kRotCap = 0.05;
+constexpr int kMaxPairs = 512;
+
 // Newton-Schulz step: V <- V - V (V^T V - I) / 2, using R and T as scratch.
 __device__ void ns_step(int d, double*& V, double*& T, double* R) {
   mm_d(d, V, true, V, R, 1.0, 0.0);
@@ -117,29 +135,49 @@ __device__ void ns_step(int d, double*& V, double*& T, double* R) {
   double* t = V; V = T; T = t;
 }
 
-__device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
+// Where the d x d matrices of one small LREP live: L1, L2 in the job's work
+// array; G, V, B, S in dynamic shared memory when 4 d^2 doubles fit, else in
+// the work array too; the FP32 copies of phase 1 alias B and S.
+struct SmallMats {
+  double *L1, *L2, *G, *V, *B, *S;
+  float *G32, *V32;
+};
+
+__device__ SmallMats small_place(const SmallJob& J, double* dyn, int dyn_bytes) {
+  const size_t dd = (size_t)J.d * J.d;
+  SmallMats m;
+  m.L1 = J.work;
+  m.L2 = J.work + dd;
+  if (4 * dd * sizeof(double) <= (size_t)dyn_bytes) {
+    m.G = dyn; m.V = dyn + dd; m.B = dyn + 2 * dd; m.S = dyn + 3 * dd;
+    m.G32 = reinterpret_cast<float*>(m.B);
+    m.V32 = reinterpret_cast<float*>(m.S);
+  } else {
+    m.G = J.work + 2 * dd; m.V = J.work + 3 * dd; m.B = J.work + 4 * dd; m.S = J.work + 5 * dd;
+    // phase 1 still runs in shared memory when its FP32 copies fit
+    const bool fit32 = 2 * dd * sizeof(float) <= (size_t)dyn_bytes;
+    m.G32 = fit32 ? reinterpret_cast<float*>(dyn) : reinterpret_cast<float*>(m.B);
+    m.V32 = fit32 ? reinterpret_cast<float*>(dyn) + dd : reinterpret_cast<float*>(m.S);
+  }
+  return m;
+}
+
+// Phase 1 of the small LREP (biorthogonality check of S, K^ = L1 L1^T,
+// M^ = L2 L2^T, G = L1^T L2, FP32 one-sided Jacobi of G) leaving G in
+// FP64 and the FP32 right factor in m.V32.  Returns false (info 1 or 2
+// written) when a Cholesky factor fails.
+__device__ bool small_phase1(const SmallJob& J, const SmallMats& mm, int* sweeps_out) {
   const int d = J.d;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   __shared__ int s_flag;
   __shared__ int s_conv;
   __shared__ double red[32];
-  __shared__ double sig[SMALL_MAXD];
-  __shared__ int perm[SMALL_MAXD];
-  __shared__ int flip[SMALL_MAXD];
-  const size_t dd = (size_t)d * d;
-  // L1, L2 in the global work array; G, V, B, S (+ float copies) in shared
-  // memory when 4 d^2 doubles fit, else in the work array too.
-  double* L1 = J.work;
-  double* L2 = J.work + dd;
-  double *G, *V, *B, *S;
-  if (4 * dd * sizeof(double) <= (size_t)dyn_bytes) {
-    G = dyn; V = dyn + dd; B = dyn + 2 * dd; S = dyn + 3 * dd;
-  } else {
-    G = J.work + 2 * dd; V = J.work + 3 * dd; B = J.work + 4 * dd; S = J.work + 5 * dd;
-  }
-  float* G32 = reinterpret_cast<float*>(B);   // phase 1 aliases B and S
-  float* V32 = reinterpret_cast<float*>(S);
+  double* L1 = mm.L1;
+  double* L2 = mm.L2;
+  double* G = mm.G;
+  float* G32 = mm.G32;
+  float* V32 = mm.V32;
   if (tid == 0) s_flag = 0;
   // biorthogonality of the current basis (safeguard input)
   if (J.S) {
@@ -159,11 +197,11 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
   __syncthreads();
   if (!chol_lower(L1, d, &s_flag)) {
     if (tid == 0) *J.info = 1;
-    return;
+    return false;
   }
   if (!chol_lower(L2, d, &s_flag)) {
     if (tid == 0) *J.info = 2;
-    return;
+    return false;
   }
   // G = L1^T L2 (both lower triangular)
   for (int e = tid; e < d * d; e += nt) {
@@ -217,6 +255,30 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
     __syncthreads();
     if (conv) break;
   }
+  *sweeps_out = sweeps;
+  return true;
+}
+
+__device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
+  const int d = J.d;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  __shared__ double red[32];
+  __shared__ double sig[SMALL_MAXD];
+  __shared__ int perm[SMALL_MAXD];
+  __shared__ int flip[SMALL_MAXD];
+  __shared__ int s_npairs, s_rot;
+  __shared__ unsigned char pa[kMaxPairs], pb[kMaxPairs];
+  const SmallMats mm = small_place(J, dyn, dyn_bytes);
+  double* L1 = mm.L1;
+  double* L2 = mm.L2;
+  double* G = mm.G;
+  double* V = mm.V;
+  double* B = mm.B;
+  double* S = mm.S;
+  const float* V32 = mm.V32;
+  int sweeps = 0;
+  if (!small_phase1(J, mm, &sweeps)) return;
   // ---- phase 2: FP64 refinement of V
   for (int e = tid; e < d * d; e += nt) V[e] = (double)V32[e];
   __syncthreads();
@@ -235,12 +297,20 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
       for (int k = 0; k < d; ++k) s = fma(B[k + i * d], B[k + j * d], s);
       S[e] = s;
     }
+    if (tid == 0) s_npairs = 0;
     __syncthreads();
+    // pairs whose 2 x 2 rotation is large (nearly equal singular values) are
+    // left to the exact sequential pass below and kept out of cmax
     for (int e = tid; e < d * d; e += nt) {
       const int i = e % d, j = e / d;
       if (i >= j) continue;
       const double aa = S[i + i * d], bb = S[j + j * d], g = S[e];
-      cmax = fmax(cmax, fabs(g) / sqrt(aa * bb));
+      if (fabs(pair_rotation(aa, bb, g)) > kRotCap) {
+        const int q = atomicAdd(&s_npairs, 1);
+        if (q < kMaxPairs) { pa[q] = (unsigned char)i; pb[q] = (unsigned char)j; }
+      } else {
+        cmax = fmax(cmax, fabs(g) / sqrt(aa * bb));
+      }
     }
     cmax = block_max(cmax, red);
     if (cmax <= tol) {
@@ -252,11 +322,8 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
       const int i = e % d, j = e / d;
       if (i >= j) continue;
       const double aa = S[i + i * d], bb = S[j + j * d], g = S[e];
-      double t = 0.0;
-      if (g != 0.0) {
-        const double zeta = (bb - aa) / (2.0 * g);
-        t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-      }
+      double t = pair_rotation(aa, bb, g);
+      if (fabs(t) > kRotCap) t = 0.0;
       S[e] = t;  // upper: +t
       S[j + i * d] = -t;  // lower: -t (distinct element, no race)
     }
@@ -270,6 +337,44 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
     ns_step(d, V, B, S);
   }
   if (!converged) mm_d(d, G, false, V, B, 1.0, 0.0);
+  // exact FP64 rotations of the nearly degenerate pairs (one warp, in order)
+  const int np = min(s_npairs, kMaxPairs);
+  if (np > 0) {
+    int left = 1;
+    for (int sw = 0; sw < 10 && left; ++sw) {
+      if (tid == 0) s_rot = 0;
+      __syncthreads();
+      if (wid == 0) {
+        for (int q = 0; q < np; ++q) {
+          const int a = pa[q], b = pb[q];
+          double al = 0.0, be = 0.0, ga = 0.0;
+          for (int i = lane; i < d; i += 32) {
+            const double x = B[i + a * d], y = B[i + b * d];
+            al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+          }
+          al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+          if (fabs(ga) > tol * sqrt(al * be)) {
+            const double t = pair_rotation(al, be, ga);
+            const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+            for (int i = lane; i < d; i += 32) {
+              const double x = B[i + a * d], y = B[i + b * d];
+              B[i + a * d] = c * x - sn * y;
+              B[i + b * d] = sn * x + c * y;
+              const double u = V[i + a * d], v = V[i + b * d];
+              V[i + a * d] = c * u - sn * v;
+              V[i + b * d] = sn * u + c * v;
+            }
+            if (lane == 0) s_rot = 1;
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      left = s_rot;
+      __syncthreads();  // every thread has read s_rot before it is reset
+    }
+    converged = converged && !left && s_npairs <= kMaxPairs;
+  }
   // singular values (column norms of B = G V), ascending order (ties by index)
   for (int j = wid; j < d; j += nw) {
     double s = 0.0;
@@ -328,7 +433,283 @@ __global__ void __launch_bounds__(SMALL_T) small_lrep_one_kernel(SmallJob J, int
   small_lrep_body(J, dyn, dyn_bytes);
 }
 
-constexpr int kSmallDynBytes = 220 * 1024;
+// ---------------------------------------------------------------- wide path
+// One small LREP spread over the GPU (single solves, d >= kWideMin): phase 1
+// (Cholesky factors, G, FP32 Jacobi) stays in one CTA; the FP64 refinement
+// of V and the Ritz coefficients run as grid kernels (every d x d product
+// over ceil(d/16)^2 CTAs), so the FP64 work uses many SMs instead of one.
+// Same arithmetic as the one-CTA path: two Newton-Schulz steps, up to six
+// steps of simultaneous rotations (+ one Newton-Schulz step each), exact
+// sequential rotations of the nearly degenerate pairs, then X^, Y^.
+// Work layout (doubles, after L1, L2): G, V, T, R, B, S (d^2 each), then the
+// control block.
+struct WideCtl {
+  unsigned long long cmax[8];  // max cos per rotation step (double bits)
+  int fail;                    // Cholesky failed: every later kernel returns
+  int stop;                    // fail or converged: refinement kernels return
+  int conv;                    // rotation steps converged
+  int npairs;                  // nearly degenerate pairs of the last step
+  int sweeps;
+  unsigned char pa[kMaxPairs], pb[kMaxPairs];
+};
+constexpr int kWideMin = 40;
+
+struct WideMats {
+  double *L1, *L2, *G, *V, *T, *R, *B, *S;
+  WideCtl* ctl;
+  int* perm;
+  double* sig;
+};
+
+__host__ __device__ inline WideMats wide_place(double* work, int d) {
+  const size_t dd = (size_t)d * d;
+  WideMats w;
+  w.L1 = work; w.L2 = work + dd; w.G = work + 2 * dd; w.V = work + 3 * dd;
+  w.T = work + 4 * dd; w.R = work + 5 * dd; w.B = work + 6 * dd; w.S = work + 7 * dd;
+  w.ctl = reinterpret_cast<WideCtl*>(work + 8 * dd);
+  w.sig = work + 8 * dd + (sizeof(WideCtl) + 7) / 8;
+  w.perm = reinterpret_cast<int*>(w.sig + d);
+  return w;
+}
+
+// phase 1 is latency bound (one pair rotation per warp per round): twice the
+// one-CTA kernel's warps
+constexpr int FRONT_T = 1024;
+
+__global__ void __launch_bounds__(FRONT_T) small_front_kernel(SmallJob J, int dyn_bytes) {
+  extern __shared__ double dyn[];
+  const int d = J.d;
+  const WideMats w = wide_place(J.work, d);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 8; ++i) w.ctl->cmax[i] = 0ull;
+    w.ctl->fail = 0; w.ctl->stop = 0; w.ctl->conv = 0; w.ctl->npairs = 0;
+  }
+  // phase 1 with G, V, B, S in shared memory when they fit (B, S hold the
+  // FP32 copies), else in the T..S slots of the work array
+  // G (FP64) in the work array; the FP32 copies of phase 1 in shared
+  // memory when they fit (d <= 166), else in the B, S slots
+  SmallMats m;
+  const size_t dd = (size_t)d * d;
+  m.L1 = w.L1; m.L2 = w.L2; m.G = w.G; m.V = w.V; m.B = w.B; m.S = w.S;
+  const bool fit32 = 2 * dd * sizeof(float) <= (size_t)dyn_bytes;
+  m.G32 = fit32 ? reinterpret_cast<float*>(dyn) : reinterpret_cast<float*>(w.B);
+  m.V32 = fit32 ? reinterpret_cast<float*>(dyn) + dd : reinterpret_cast<float*>(w.S);
+  int sweeps = 0;
+  const bool ok = small_phase1(J, m, &sweeps);
+  if (!ok) {
+    if (threadIdx.x == 0) { w.ctl->fail = 1; w.ctl->stop = 1; }
+    return;
+  }
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) w.V[e] = (double)m.V32[e];
+  if (threadIdx.x == 0) w.ctl->sweeps = sweeps;
+}
+
+// C = alpha op(A) B + beta D + gamma I (d x d, ld d); 16 x 16 tile per CTA.
+__global__ void __launch_bounds__(256) sq_gemm_kernel(int d, const double* __restrict__ A,
+                                                      int transA, const double* __restrict__ B,
+                                                      double* __restrict__ C, double alpha,
+                                                      const double* __restrict__ D, double beta,
+                                                      double gamma, const int* __restrict__ skip) {
+  if (*skip) return;
+  __shared__ double As[16][17], Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i = blockIdx.x * 16 + tx, j = blockIdx.y * 16 + ty;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < d; k0 += 16) {
+    // As[kk][ii] = op(A)[blockIdx.x*16 + ii][k0 + kk]; Bs[jj][kk] = B[k0 + kk][blockIdx.y*16 + jj]
+    {
+      const int ii = tx, kk = ty;
+      const int r = blockIdx.x * 16 + ii, k = k0 + kk;
+      double a = 0.0;
+      if (r < d && k < d) a = transA ? A[k + (size_t)r * d] : A[r + (size_t)k * d];
+      As[kk][ii] = a;
+      const int kb = k0 + tx, cb = blockIdx.y * 16 + ty;
+      Bs[ty][tx] = (kb < d && cb < d) ? B[kb + (size_t)cb * d] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc = fma(As[kk][tx], Bs[ty][kk], acc);
+    __syncthreads();
+  }
+  if (i < d && j < d) {
+    double v = alpha * acc;
+    if (D) v = fma(beta, D[i + (size_t)j * d], v);
+    if (i == j) v += gamma;
+    C[i + (size_t)j * d] = v;
+  }
+}
+
+// Rotation step: from S = B^T B (full, ld d) the tangents t of the pairs
+// (Omega, upper +t / lower -t, zero diagonal, |t| <= kRotCap), the largest
+// cosine of the capped pairs into ctl->cmax[it], the other pairs into the
+// degenerate list.
+__global__ void __launch_bounds__(256) sq_rot_kernel(int d, const double* __restrict__ S,
+                                                     double* __restrict__ Om, WideCtl* ctl,
+                                                     int it) {
+  if (ctl->stop) return;
+  __shared__ double red[8];
+  double cmax = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d * d; e += gridDim.x * blockDim.x) {
+    const int i = e % d, j = e / d;
+    if (i == j) { Om[e] = 0.0; continue; }
+    const int a = min(i, j), b = max(i, j);
+    const double aa = S[a + (size_t)a * d], bb = S[b + (size_t)b * d], g = S[a + (size_t)b * d];
+    double t = pair_rotation(aa, bb, g);
+    if (fabs(t) > kRotCap) {
+      t = 0.0;
+      if (i < j) {
+        const int q = atomicAdd(&ctl->npairs, 1);
+        if (q < kMaxPairs) { ctl->pa[q] = (unsigned char)a; ctl->pb[q] = (unsigned char)b; }
+      }
+    } else if (i < j) {
+      cmax = fmax(cmax, fabs(g) / sqrt(aa * bb));
+    }
+    Om[e] = (i < j) ? t : -t;
+  }
+  for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) cmax = fmax(cmax, red[w]);
+    atomicMax(&ctl->cmax[it], (unsigned long long)__double_as_longlong(cmax));
+  }
+}
+
+// after sq_rot_kernel(it): converged when the largest capped cosine is
+// below tol; otherwise clear the pair list for the next step
+__global__ void sq_check_kernel(WideCtl* ctl, int it, double tol, int last) {
+  if (ctl->stop) return;
+  if (__longlong_as_double((long long)ctl->cmax[it]) <= tol) {
+    ctl->stop = 1;
+    ctl->conv = 1;
+  } else if (!last) {
+    ctl->npairs = 0;
+  }
+}
+
+__global__ void sq_copy_kernel(int cnt, const double* __restrict__ src, double* __restrict__ dst,
+                               const int* __restrict__ skip) {
+  if (*skip) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
+// exact rotations of the degenerate pairs (B = G V, V), singular values and
+// their ascending order, eigenvalues (one CTA)
+__global__ void __launch_bounds__(SMALL_T) sq_final_kernel(SmallJob J, double tol) {
+  const int d = J.d;
+  const WideMats w = wide_place(J.work, d);
+  WideCtl* ctl = w.ctl;
+  if (ctl->fail) return;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5,
+            nw = nt >> 5;
+  __shared__ int s_rot;
+  double* B = w.B;
+  double* V = w.V;
+  const int np = min(ctl->npairs, kMaxPairs);
+  int left = 0;
+  if (np > 0) {
+    left = 1;
+    for (int sw = 0; sw < 10 && left; ++sw) {
+      if (tid == 0) s_rot = 0;
+      __syncthreads();
+      if (wid == 0) {
+        for (int q = 0; q < np; ++q) {
+          const int a = ctl->pa[q], b = ctl->pb[q];
+          double al = 0.0, be = 0.0, ga = 0.0;
+          for (int i = lane; i < d; i += 32) {
+            const double x = B[i + a * d], y = B[i + b * d];
+            al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+          }
+          al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+          if (fabs(ga) > tol * sqrt(al * be)) {
+            const double t = pair_rotation(al, be, ga);
+            const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+            for (int i = lane; i < d; i += 32) {
+              const double x = B[i + a * d], y = B[i + b * d];
+              B[i + a * d] = c * x - sn * y;
+              B[i + b * d] = sn * x + c * y;
+              const double u = V[i + a * d], v = V[i + b * d];
+              V[i + a * d] = c * u - sn * v;
+              V[i + b * d] = sn * u + c * v;
+            }
+            if (lane == 0) s_rot = 1;
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      left = s_rot;
+      __syncthreads();
+    }
+  }
+  for (int j = wid; j < d; j += nw) {
+    double s = 0.0;
+    for (int i = lane; i < d; i += 32) s = fma(B[i + j * d], B[i + j * d], s);
+    s = warp_sum(s);
+    if (lane == 0) w.sig[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = tid; j < d; j += nt) {
+    int rk = 0;
+    const double sj = w.sig[j];
+    for (int k = 0; k < d; ++k) rk += (w.sig[k] < sj) || (w.sig[k] == sj && k < j);
+    w.perm[rk] = j;
+  }
+  __syncthreads();
+  for (int i = tid; i < d; i += nt) J.lam[i] = w.sig[w.perm[i]];
+  if (tid == 0) {
+    *J.info = (ctl->conv && !left && ctl->npairs <= kMaxPairs) ? 0 : 3;
+    if (J.sweeps) *J.sweeps = ctl->sweeps;
+  }
+}
+
+// X^ = L2 V S^-1/2, Y^ = L1 W S^-1/2 with W = B / S (grid)
+__global__ void __launch_bounds__(256) sq_assemble_kernel(SmallJob J) {
+  const int d = J.d;
+  const WideMats w = wide_place(J.work, d);
+  if (w.ctl->fail) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d * d; e += gridDim.x * blockDim.x) {
+    const int r = e % d, i = e / d;
+    const int j = w.perm[i];
+    const double s = w.sig[j];
+    double x = 0.0, y = 0.0;
+    for (int k = 0; k <= r; ++k) {
+      x = fma(w.L2[r + k * d], w.V[k + j * d], x);
+      y = fma(w.L1[r + k * d], w.B[k + j * d], y);
+    }
+    J.Xh[r + (size_t)i * J.ldo] = x / sqrt(s);
+    J.Yh[r + (size_t)i * J.ldo] = y / (s * sqrt(s));
+  }
+}
+
+// sign of each Ritz pair follows its previous iterate (X^[j, j] >= 0)
+__global__ void __launch_bounds__(256) sq_flip_kernel(SmallJob J) {
+  const int d = J.d;
+  const WideMats w = wide_place(J.work, d);
+  if (w.ctl->fail) return;
+  const int wa = min(J.w_prev, d);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d * wa; e += gridDim.x * blockDim.x) {
+    const int r = e % d, i = e / d;
+    if (J.Xh[i + (size_t)i * J.ldo] < 0.0 && r != i) {
+      J.Xh[r + (size_t)i * J.ldo] = -J.Xh[r + (size_t)i * J.ldo];
+      J.Yh[r + (size_t)i * J.ldo] = -J.Yh[r + (size_t)i * J.ldo];
+    }
+  }
+}
+__global__ void sq_flip_diag_kernel(SmallJob J) {
+  const int d = J.d;
+  const WideMats w = wide_place(J.work, d);
+  if (w.ctl->fail) return;
+  const int wa = min(J.w_prev, d);
+  for (int i = threadIdx.x; i < wa; i += blockDim.x)
+    if (J.Xh[i + (size_t)i * J.ldo] < 0.0) {
+      J.Xh[i + (size_t)i * J.ldo] = -J.Xh[i + (size_t)i * J.ldo];
+      J.Yh[i + (size_t)i * J.ldo] = -J.Yh[i + (size_t)i * J.ldo];
+    }
+}
+
+constexpr int kSmallDynBytes = 216 * 1024;
 
 cudaError_t small_smem_setup() {
   static const cudaError_t once = [] {
@@ -337,9 +718,54 @@ cudaError_t small_smem_setup() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(small_lrep_one_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallDynBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(small_front_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallDynBytes);
     return e;
   }();
   return once;
+}
+
+cudaError_t small_lrep_wide(const SmallJob& J, cudaStream_t st) {
+  const int d = J.d;
+  const WideMats w = wide_place(J.work, d);
+  const int* fail = &w.ctl->fail;
+  const int* stop = &w.ctl->stop;
+  const double tol = (double)d * 2.220446049250313e-16;
+  const dim3 g((d + 15) / 16, (d + 15) / 16);
+  const unsigned ge = (unsigned)std::min(256, (d * d + 255) / 256);
+  small_front_kernel<<<1, FRONT_T, kSmallDynBytes, st>>>(J, kSmallDynBytes); LREP_COUNT_LAUNCH();
+  auto gemm = [&](const double* A, int tA, const double* B, double* C, double alpha,
+                  const double* D, double beta, double gamma, const int* skip) {
+    sq_gemm_kernel<<<g, 256, 0, st>>>(d, A, tA, B, C, alpha, D, beta, gamma, skip);
+    LREP_COUNT_LAUNCH();
+  };
+  auto copy = [&](const double* src, double* dst, const int* skip) {
+    sq_copy_kernel<<<ge, 256, 0, st>>>(d * d, src, dst, skip); LREP_COUNT_LAUNCH();
+  };
+  // Newton-Schulz: R = V^T V - I, T = V - V R / 2, V = T
+  auto ns = [&](const int* skip) {
+    gemm(w.V, 1, w.V, w.R, 1.0, nullptr, 0.0, -1.0, skip);
+    gemm(w.V, 0, w.R, w.T, -0.5, w.V, 1.0, 0.0, skip);
+    copy(w.T, w.V, skip);
+  };
+  ns(fail);
+  ns(fail);
+  for (int it = 0; it < 6; ++it) {
+    gemm(w.G, 0, w.V, w.B, 1.0, nullptr, 0.0, 0.0, stop);   // B = G V
+    gemm(w.B, 1, w.B, w.S, 1.0, nullptr, 0.0, 0.0, stop);   // S = B^T B
+    sq_rot_kernel<<<ge, 256, 0, st>>>(d, w.S, w.R, w.ctl, it); LREP_COUNT_LAUNCH();
+    sq_check_kernel<<<1, 1, 0, st>>>(w.ctl, it, tol, it == 5); LREP_COUNT_LAUNCH();
+    gemm(w.V, 0, w.R, w.T, 1.0, w.V, 1.0, 0.0, stop);       // T = V + V Omega
+    copy(w.T, w.V, stop);
+    ns(stop);
+  }
+  gemm(w.G, 0, w.V, w.B, 1.0, nullptr, 0.0, 0.0, fail);     // B = G V
+  sq_final_kernel<<<1, SMALL_T, 0, st>>>(J, tol); LREP_COUNT_LAUNCH();
+  sq_assemble_kernel<<<ge, 256, 0, st>>>(J); LREP_COUNT_LAUNCH();
+  sq_flip_kernel<<<ge, 256, 0, st>>>(J); LREP_COUNT_LAUNCH();
+  sq_flip_diag_kernel<<<1, 256, 0, st>>>(J); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- eq. hat_pq
@@ -585,7 +1011,9 @@ cudaError_t chol_upper_inverse(int r, const double* G, int ldg, double* Cinv,
   return cudaGetLastError();
 }
 
-size_t small_work_elems(int d) { return (size_t)6 * d * d; }
+size_t small_work_elems(int d) {
+  return (size_t)8 * d * d + (sizeof(WideCtl) + 7) / 8 + 2 * (size_t)d + 64;
+}
 
 cudaError_t small_lrep_batched(const SmallJob* jobs_dev, int njobs, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
@@ -595,10 +1023,13 @@ cudaError_t small_lrep_batched(const SmallJob* jobs_dev, int njobs, cudaStream_t
   return cudaGetLastError();
 }
 
+int small_wide_min() { return kWideMin; }
+
 cudaError_t small_lrep_one(const SmallJob& job, cudaStream_t st) {
   if (job.d <= 0 || job.d > SMALL_MAXD) return cudaErrorInvalidValue;
   cudaError_t e = small_smem_setup();
   if (e != cudaSuccess) return e;
+  if (job.d >= kWideMin) return small_lrep_wide(job, st);
   small_lrep_one_kernel<<<1, SMALL_T, kSmallDynBytes, st>>>(job, kSmallDynBytes); LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }

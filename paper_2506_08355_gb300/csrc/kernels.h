@@ -129,6 +129,9 @@ struct SmallJob {
 size_t small_work_elems(int d);
 cudaError_t small_lrep_batched(const SmallJob* jobs_dev, int njobs, cudaStream_t st);
 cudaError_t small_lrep_one(const SmallJob& job, cudaStream_t st);
+// small_lrep_one spreads orders d >= this over the grid (FP64 refinement as
+// multi-CTA products); below it, one CTA (as in small_lrep_batched)
+int small_wide_min();
 
 // eq. hat_pq + small Alg. 1 (one CTA).
 struct PqJob {

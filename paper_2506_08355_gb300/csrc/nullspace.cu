@@ -142,7 +142,7 @@ struct NullFinder {
     Arena dry;
     dry.cap = ~(size_t)0;
     layout(dry);
-    NCK(A.reserve(dry.off + 4096));
+    NCK(A.reserve(dry.off + 4096, st));
     A.off = 0;
     layout(A);
     return LREP_OK;

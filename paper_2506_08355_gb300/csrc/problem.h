@@ -16,11 +16,12 @@ struct OzOperand;
 
 enum OpKind { OP_DENSE = 0, OP_CSR = 1, OP_STENCIL = 2, OP_CALLBACK = 3 };
 
-// Device arena: one cudaMalloc, bump allocation, zero-filled.
+// Device arena: one cudaMalloc, bump allocation, zero-filled on the stream
+// that uses it.
 struct Arena {
   char* base = nullptr;
   size_t cap = 0, off = 0;
-  cudaError_t reserve(size_t bytes);
+  cudaError_t reserve(size_t bytes, cudaStream_t st);
   template <class T>
   T* take(size_t count) {
     const size_t a = 256;

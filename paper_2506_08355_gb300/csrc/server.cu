@@ -8,10 +8,12 @@
 //  * Overlap: every slot is a host thread with its own CUDA stream; the
 //    solve of an admitted request runs on its slot's stream, so the work of
 //    concurrent requests overlaps on the device.
-//  * Shared launches: the small projected problems (eq. small_eigen) of all
-//    running solves meet at a rendezvous and are solved by one batched
-//    launch, one CTA per request.  Each CTA's arithmetic does not depend on
-//    the batch, so a result is the same alone and in a mix.
+//  * Shared launches: the small projected problems (eq. small_eigen) of
+//    order < 40 of all running solves meet at a rendezvous and are solved by
+//    one batched launch, one CTA per request; larger ones run in their
+//    multi-CTA form on the requester's stream (concurrent requests fill the
+//    GPU).  Neither form's arithmetic depends on the batch, so a request's
+//    result is the same alone, in a mix, or through a direct lrep_solve.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -89,6 +91,9 @@ struct Batcher : SmallBatcher {
   }
 
   cudaError_t run(const SmallJob& job, cudaStream_t st) override {
+    // orders that the grid-wide form serves better are not batched: they
+    // run on the requester's stream, with the arithmetic of a direct solve
+    if (job.d >= small_wide_min()) return small_lrep_one(job, st);
     Waiter me;
     me.job = job;
     me.st = st;

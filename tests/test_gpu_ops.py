@@ -135,6 +135,32 @@ def test_small_lrep(L, d):
     np.testing.assert_allclose(Xg.T @ Yg, np.eye(d), atol=1e-11)
 
 
+@pytest.mark.parametrize("d,mult", [(40, 4), (80, 2), (24, 24)])
+def test_small_lrep_degenerate(L, d, mult):
+    """Repeated eigenvalues (K^ M^ with a `mult`-fold eigenvalue, and the
+    fully degenerate K^ = M^ = 2 I): the eigenvalues are unique, the pairs
+    inside a cluster are not; check the values, K^ X^ = Y^ Lam,
+    M^ Y^ = X^ Lam and X^T Y^ = I."""
+    import torch
+    rng = np.random.default_rng(100 + d + mult)
+    Q, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    ev = np.concatenate([np.full(mult, 1.5), rng.uniform(2.0, 9.0, d - mult)])
+    if mult == d:
+        ev = np.full(d, 2.0)
+    A = (Q * ev) @ Q.T          # K^ = M^ = A: eigenvalues of K^ M^ are ev^2
+    lam = torch.zeros(d, dtype=torch.float64, device="cuda")
+    Xh = torch.zeros((d, d), dtype=torch.float64, device="cuda")
+    Yh = torch.zeros((d, d), dtype=torch.float64, device="cuda")
+    info = L.small_lrep(to_dev(A), to_dev(A), lam, Xh, Yh)
+    assert info == 0
+    lg, Xg, Yg = lam.cpu().numpy(), from_dev(Xh), from_dev(Yh)
+    np.testing.assert_allclose(lg, np.sort(ev), rtol=1e-12)
+    sc = np.abs(A).max() * max(1.0, np.abs(Xg).max())
+    np.testing.assert_allclose(A @ Xg, Yg * lg, atol=1e-11 * sc)
+    np.testing.assert_allclose(A @ Yg, Xg * lg, atol=1e-11 * sc)
+    np.testing.assert_allclose(Xg.T @ Yg, np.eye(d), atol=1e-11)
+
+
 def test_small_lrep_not_spd(L):
     import torch
     d = 6

@@ -1,8 +1,9 @@
 """Serving: continuous batching of concurrent solves (lrep_server_*).
 
-Each result must be the same alone and in the mix: the small projected
-problems of concurrent solves share launches, but every reduction has a
-fixed order, so the eigenpairs agree to the last bit (checked to 1e-14).
+Each result must be the same alone (a direct solve) and in the mix: the
+small projected problems of concurrent solves share launches, but every
+reduction has a fixed order, so the eigenpairs agree to the last bit
+(checked to 1e-14).
 """
 import numpy as np
 import pytest
@@ -20,9 +21,11 @@ def L(built_lib):
 
 
 def _requests():
-    # (n, nev, block, precision, seed)
+    # (n, nev, block, precision, seed); the last has a projected problem of
+    # order 48 (grid-wide small LREP), the others below 40 (batched)
     return [(300, 4, 4, 0, 21), (512, 8, 8, 1, 22), (400, 16, 4, 0, 23),
-            (640, 4, 4, 1, 24), (350, 8, 8, 0, 25), (700, 12, 4, 0, 26)]
+            (640, 4, 4, 1, 24), (350, 8, 8, 0, 25), (700, 12, 4, 0, 26),
+            (900, 16, 16, 3, 27)]
 
 
 def _make(L, n, prec, seed):
