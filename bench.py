@@ -2,7 +2,8 @@
 """Throughput of the GB300 BOSP solver: eigenpairs/s at residual <= tol.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision fp64|mixed|sliced|mixed-sliced]
+                    [--precision fp64|mixed|sliced|mixed-sliced] [--compare P]
+                    [--config 1|2|3] [--op ...] [--serve ...]
 
 One step is one complete solve (Alg. 2 with the moving window) of the dense
 n = 8192 workload: K, M built from chosen spectra with Haar bases, k and m
@@ -13,10 +14,15 @@ L2, so no flush is needed between steps.  value = eigenpairs per second
 over the K timed steps (all ranks; every rank solves its own replica, the
 solver does not shard: "replicas only").
 
-Also reported: the dominant kernel's roofline (the float64 dense product,
-timed per launch with CUDA events on the solver's stream), an end-to-end
-figure through the C ABI from pinned host buffers, the CPU oracle as a
-baseline, and the SM clocks sampled during the timed region.
+Default precision: mixed-sliced (bf16 hi/lo operator for the inexact CG
+solves, float64-accurate products, Grams and updates on the tensor cores by
+error-free slicing; every returned pair re-checked at residual <= tol).
+The 'compare' entry times the same workload with the FP64 kernels.
+
+Also reported: the dominant kernel's roofline (timed per launch with CUDA
+events on the solver's stream), an end-to-end figure through the C ABI from
+pinned host buffers, the CPU oracle as a baseline, and the SM clocks sampled
+during the timed region.
 """
 from __future__ import annotations
 
@@ -48,7 +54,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
+    ap.add_argument("--precision", default="mixed-sliced", choices=list(PRECISIONS))
+    ap.add_argument("--compare", default="fp64", choices=list(PRECISIONS) + ["none"],
+                    help="also time this precision on the same problem (3 warm-up "
+                         "solves, 1 timed) for the line's 'compare' entry")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--op", default=None, choices=["dense", "tc", "sliced", "small", "stencil", "gram"],
@@ -155,7 +164,9 @@ def workload(precision, config=1):
     if config == 3:
         p = synth.haar_dense_device(32768, seed=3, k_range=(1e-2, 1e2), m_range=(1e-2, 1e2),
                                     law="loguniform")
-        p.update(nev=256, block=32, tol=1e-8, X0=None)
+        # 256 pairs in windows of 32 at condition 1e4 take ~1000 outer
+        # iterations (CG at its 20-iteration cap)
+        p.update(nev=256, block=32, tol=1e-8, X0=None, maxit=5000)
         return p, {"workload": "dense-lrep-n32768-nev256-block32-tol1e-8",
                    "n": 32768, "nev": 256, "block": 32, "tol": 1e-8, "nullspace": 0,
                    "spectra": "k, m log-uniform [1e-2, 1e2], Haar Q1, Q2 (seed 3, device)",
@@ -461,7 +472,7 @@ def main():
     if p.get("X0") is not None:
         X0 = p["X0"]
         prob.set_nullspace(X0 if isinstance(X0, np.ndarray) else X0.T.contiguous())
-    prob.set_options(precision=prec, profile=0)
+    prob.set_options(precision=prec, profile=0, maxit=p.get("maxit", 500))
     for _ in range(args.warmup):
         st = prob.solve(nev, nb, tol)
         assert st == lrep.OK, st
@@ -490,13 +501,16 @@ def main():
     ms_step = ms / args.steps
     res = prob.residuals()
     assert prob.nconv() == nev and res.max() < tol, (prob.nconv(), res.max())
+    ph = prob.timings()  # last timed solve, Table 6 buckets (device events)
+    phases = {"init_U_V": ph[0], "grams_small_lrep_pullback": ph[1],
+              "convergence_check": ph[2], "P_Q": ph[3], "W_Z_cg_projection": ph[4]}
     # roofline of the dominant kernel: one more profiled solve (per-launch
     # CUDA events on the solver's stream)
-    prob.set_options(precision=prec, profile=1)
+    prob.set_options(precision=prec, profile=1, maxit=p.get("maxit", 500))
     prob.solve(nev, nb, tol)
     prof_all = np.asarray(prob.profile())
     prof_cg = np.asarray(prob.profile_cg())
-    prob.set_options(precision=prec, profile=0)
+    prob.set_options(precision=prec, profile=0, maxit=p.get("maxit", 500))
     # the dominant product class by device time: CG-operator products or
     # the float64-accurate products
     cg_dominant = prof_cg[0] >= prof_all[0] - prof_cg[0]
@@ -527,6 +541,29 @@ def main():
             "hbm_gbs_achieved": bytes_launch / avg_s / 1e9,
             "hbm_frac_of_measured": (bytes_launch / avg_s / 1e9) / hbm_peak,
             "peak_note": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak); HBM of measured"}
+    # the same workload with another precision (default: the FP64 kernels)
+    compare = None
+    if args.compare != "none" and args.compare != args.precision:
+        cprec = PRECISIONS[args.compare]
+        if (cprec & PRECISIONS["mixed"]) and args.config == 2:
+            cprec = None  # the bf16 CG operator needs a dense operator
+        if cprec is not None:
+            prob.set_options(precision=cprec, profile=0, maxit=p.get("maxit", 500))
+            for _ in range(3):
+                assert prob.solve(nev, nb, tol) == lrep.OK
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            assert prob.solve(nev, nb, tol) == lrep.OK
+            c1.record(stream)
+            torch.cuda.synchronize()
+            cms = c0.elapsed_time(c1)
+            compare = {"precision": args.compare, "value": nev / (cms * 1e-3),
+                       "unit": "eigenpairs/s", "ms_per_step": cms, "steps": 1, "warmup": 3,
+                       "outer_iterations": prob.iters(),
+                       "max_residual": float(prob.residuals().max())}
+            prob.set_options(precision=prec, profile=0, maxit=p.get("maxit", 500))
     # end to end through the public API from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -571,7 +608,8 @@ def main():
                 "dtype": DTYPES[args.precision],
                 "data": "synthetic", "config": cfg,
                 "outer_iterations": iters, "max_residual": float(res.max()),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "phase_seconds_per_solve": phases,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "compare": compare,
                 "gpu_launches": int(launches), "clocks": clk,
                 "parallelism": "replicas only (%d)" % world}
         print(json.dumps(line), flush=True)

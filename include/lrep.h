@@ -60,21 +60,24 @@ enum { LREP_MEM_HOST = 0, LREP_MEM_DEVICE_COPY = 1, LREP_MEM_DEVICE_BORROW = 2 }
  * LREP_FORM_KM: inputs are K and M directly. */
 enum { LREP_FORM_AB = 0, LREP_FORM_KM = 1 };
 enum { LREP_OP_K = 0, LREP_OP_M = 1 };
-/* Arithmetic of the operator products K X, M Y (dense operators only for
- * anything but FP64; two independent bits).
+/* Arithmetic of the float64-accurate work and of the CG products (two
+ * independent bits; bit 0 needs a dense operator).
  * FP64: every product in float64 (FP64 FMA units).
  * MIXED_BF16X3 (bit 0): the inexact CG products of eq. block_GS use K, M
  *   split as hi + lo bfloat16 pairs (three bf16 tensor-core products, fp32
  *   accumulation); every product that enters H^ (eq. hat_H) and every
  *   residual (eq. tol) keeps float64 accuracy.
- * FP64_SLICED (bit 1): the float64-accurate products (and, without bit 0,
- *   the CG products too) run on the bf16 tensor cores by error-free
- *   slicing: K, M and each X held as seven base-2^8 digit planes under
- *   power-of-two row / column scales, the 28 leading digit-pair products
- *   summed exactly in integer arithmetic (levels 2..5) or in fp32 (levels
- *   6..8, weight <= 2^-48).  Error <= ~2^-54.7 n 2^(e_i + f_j) per entry,
- *   2^e_i and 2^f_j bounding row i of K (M) and column j of X: the form of
- *   the float64 product's own bound.  Holds 14 bytes per matrix entry.
+ * FP64_SLICED (bit 1): the float64-accurate dense products (and, without
+ *   bit 0, the CG products too) and, for every operator kind, the large
+ *   tall-skinny Grams and block updates of the solve run on the bf16 tensor
+ *   cores by error-free slicing: each factor held as seven base-2^8 digit
+ *   planes under power-of-two row / column scales, the 28 leading
+ *   digit-pair products summed exactly in integer arithmetic (levels 2..5)
+ *   or in fp32 (levels 6..8, weight <= 2^-48).  Error <= ~2^-54.7 k
+ *   2^(e_i + f_j) per entry (k the contracted length, 2^e_i and 2^f_j
+ *   bounding row i of the left and column j of the right factor): the form
+ *   of the float64 product's own bound.  Holds 14 bytes per dense K, M
+ *   entry.
  * MIXED_SLICED = both bits. */
 enum {
   LREP_PREC_FP64 = 0,

@@ -51,6 +51,28 @@ lrep_status lrep_op_update(int64_t n, int32_t k, int32_t c, double alpha,
                            int64_t ldb, double beta, double* C, int64_t ldc,
                            void* stream);
 
+/* lrep_op_gram and lrep_op_update with float64 accuracy on the bf16 tensor
+ * cores (error-free slicing, the route of precision FP64_SLICED): every
+ * column of A and B (Gram), every row of A and column of B (update) is
+ * written as a power-of-two scale times seven base-2^8 digits, and the 28
+ * leading digit-pair products are summed exactly (or, below 2^-48 of the
+ * scale, in fp32).  Error <= ~2^-54.7 * k * 2^(e_i + f_j), k the contracted
+ * length, 2^e_i and 2^f_j bounding row i of the left and column j of the
+ * right factor: the form of the float64 product's bound.  For the update,
+ * 1 <= k <= 768 and beta != 0.  Synchronises `stream` (reads the kernels'
+ * timeout flag); LREP_ERR_CUDA if a tensor-core pipeline wait expired.
+ * Not in the paper: a GB300 device for its Grams (eq. hat_H) and block
+ * updates (eq. eigenVector-pullback, eq. update_W/Z), FP64 being its
+ * scarcest unit. */
+lrep_status lrep_op_gram_sliced(int64_t n, int32_t a, int32_t b,
+                                const double* A, int64_t lda, const double* B,
+                                int64_t ldb, double* G, int64_t ldg,
+                                void* stream);
+lrep_status lrep_op_update_sliced(int64_t n, int32_t k, int32_t c,
+                                  double alpha, const double* A, int64_t lda,
+                                  const double* B, int64_t ldb, double beta,
+                                  double* C, int64_t ldc, void* stream);
+
 /* Small projected LREP (eq. small_eigen) of order d <= 256: K^, M^ are
  * d x d (leading dimension ld; symmetrised as (G + G^T)/2).  Writes the d
  * eigenvalues ascending to lam[d] and X^, Y^ (d x d, leading dimension

@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "oz.h"
 #include "problem.h"
 
 namespace lrep {
@@ -135,6 +136,10 @@ struct Solver {
   // scratch for reductions and split-K
   double* ws;
   size_t ws_elems = 0, part_elems = 0;
+  // sliced (tensor-core, float64-accurate) Grams and updates
+  bool oz = false;
+  uint8_t* ozws = nullptr;
+  size_t ozws_bytes = 0;
   double* part;
   double *Rg, *Rinv, *Rwork;  // r x r scratch of the V0 normalisation
   unsigned int* counters;  // [0] residual [1] colnorm [2..4] cg
@@ -236,6 +241,7 @@ struct Solver {
     info_d = A.take<int>(64); cnt_d = A.take<int>(64); act_d = A.take<int>(64);
     ws = A.take<double>(std::max<size_t>(ws_elems, 1));
     part = A.take<double>(std::max<size_t>(part_elems, 1));
+    ozws = oz ? A.take<uint8_t>(ozws_bytes) : nullptr;
     counters = A.take<unsigned int>(64);
     cg.rho = A.take<double>(cgcols); cg.stop = A.take<double>(cgcols);
     cg.alpha = A.take<double>(cgcols); cg.beta = A.take<double>(cgcols);
@@ -260,6 +266,16 @@ struct Solver {
     wsz = std::max(wsz, gram_ws_elems(n, nev, nev));
     wsz = std::max(wsz, apply_ws_elems(p, std::max(C, cgcols)));
     ws_elems = wsz;
+    oz = (p->opts.precision & LREP_PREC_FP64_SLICED) != 0;
+    if (oz) {
+      size_t b = 0;
+      const int shapes[5][2] = {{dmax, dmax}, {dd, dd}, {Lmax, cgcols},
+                                {rr, std::max(rr, dmax)}, {nev, nev}};
+      for (const auto& sh : shapes) b = std::max(b, oz_gram_ws_bytes(n, sh[0], sh[1]));
+      const int kmax = std::max(std::max(dmax, dd), std::max(Lmax, rr));
+      b = std::max(b, oz_update_ws_bytes(n, kmax, std::max(dmax, std::max(cgcols, nev))));
+      ozws_bytes = b + 512;
+    }
     part_elems = std::max(residual_ws_elems(n, std::max(C, nev)),
                           std::max(colnorm_ws_elems(n, cgcols), cg_part_elems(n, cgcols)));
     Arena dry;
@@ -296,12 +312,24 @@ struct Solver {
   }
 
   // ---------------------------------------------------------- primitives
+  // float64-accurate products below this many flops stay on the FP64 units
+  // (the sliced form costs ~5 launches)
+  static constexpr double kSlicedMinFlops = 1.6e7;
   lrep_status gram(const Segs& A, const Segs& B, double* G, int64_t ldg) {
+    if (oz && 2.0 * n * A.total() * B.total() >= kSlicedMinFlops) {
+      LCK(oz_gram(n, A, B, G, ldg, ozws, ozws_bytes, p->op.tc_err, st));
+      return LREP_OK;
+    }
     LCK(gram_f64(n, A, B, G, ldg, ws, ws_elems, st));
     return LREP_OK;
   }
   lrep_status update(int c, double alpha, const Segs& A, const double* B,
                      int64_t ldb, double beta, double* Cm) {
+    if (oz && beta != 0.0 && 2.0 * n * A.total() * c >= kSlicedMinFlops) {
+      LCK(oz_update(n, A.total(), c, alpha, A, B, ldb, beta, Cm, ld, ozws, ozws_bytes,
+                    p->op.tc_err, st));
+      return LREP_OK;
+    }
     LCK(update_f64(n, c, alpha, A, B, ldb, beta, Cm, ld, st));
     return LREP_OK;
   }
@@ -540,6 +568,21 @@ struct Solver {
     return LREP_OK;
   }
 
+  // Rayleigh-Ritz with one recovery: K^ or M^ that fails to be positive
+  // definite (products carried by recurrence drifted, or U, V lost
+  // biorthogonality) is retried once from fresh products of a
+  // re-biorthogonalised basis.
+  lrep_status rayleigh_ritz_safe(int* e) {
+    lrep_status s = rayleigh_ritz(*e);
+    if (s != LREP_ERR_NOT_SPD) return s;
+    p->err.clear();
+    LST(refresh());
+    LST(rebiorth());
+    LST(refresh());
+    *e = std::min(d, std::min(w, d) + (moving ? 2 * nb : 0));
+    return rayleigh_ritz(*e);
+  }
+
   // safeguard: Step 2's biorthogonalisation applied to the current U, V;
   // K U and M V follow by the same combinations.
   lrep_status rebiorth() {
@@ -577,12 +620,12 @@ struct Solver {
       if (it > 1 && it % every == 0) LST(refresh());
       const int want_max = std::min(w, d);
       int e = std::min(d, want_max + (moving ? 2 * nb : 0));
-      LST(rayleigh_ritz(e));
+      LST(rayleigh_ritz_safe(&e));
       if (h->berr > p->opts.rebiorth_tol) {
         LST(rebiorth());
         LST(refresh());
         e = std::min(d, std::min(w, d) + (moving ? 2 * nb : 0));
-        LST(rayleigh_ritz(e));
+        LST(rayleigh_ritz_safe(&e));
       }
       int wv = std::min(w, d);
       int want = std::min(wv, nev - ell);
@@ -593,7 +636,7 @@ struct Solver {
         // decisions are taken on freshly computed products
         LST(refresh());
         e = std::min(d, std::min(w, d) + (moving ? 2 * nb : 0));
-        LST(rayleigh_ritz(e));
+        LST(rayleigh_ritz_safe(&e));
         wv = std::min(w, d);
         want = std::min(wv, nev - ell);
         c = 0;

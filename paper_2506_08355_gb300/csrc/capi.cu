@@ -9,6 +9,7 @@
 
 #include "../../include/lrep.h"
 #include "../../include/lrep_ops.h"
+#include "oz.h"
 #include "problem.h"
 
 using namespace lrep;
@@ -319,8 +320,8 @@ lrep_status lrep_set_options(lrep_problem p, const lrep_options* o) {
       !(o->discard_tol >= 0.0) || o->refresh_every < 1 || !(o->rebiorth_tol > 0.0) ||
       o->precision < LREP_PREC_FP64 || o->precision > LREP_PREC_MIXED_SLICED)
     return p->fail(LREP_ERR_ARG, "lrep_set_options: invalid value");
-  if (o->precision != LREP_PREC_FP64 && p->op.kind != OP_DENSE)
-    return p->fail(LREP_ERR_ARG, "tensor-core precisions need a dense operator");
+  if ((o->precision & LREP_PREC_MIXED_BF16X3) && p->op.kind != OP_DENSE)
+    return p->fail(LREP_ERR_ARG, "the bf16 hi/lo CG operator needs a dense operator");
   const bool rebuild = (o->precision != p->opts.precision);
   p->opts = *o;
   if (rebuild) {
@@ -489,6 +490,75 @@ lrep_status lrep_op_gram(int64_t n, int32_t a, int32_t b, const double* A, int64
   cudaError_t e = gram_f64(n, seg1(A, lda, a), seg1(B, ldb, b), G, ldg, ws, need,
                            (cudaStream_t)stream);
   return e == cudaSuccess ? LREP_OK : cuda_fail(nullptr, "lrep_op_gram", e);
+}
+
+// device word for the timeout flag of the sliced kernels (one per device)
+int* sliced_err_flag(void* stream) {
+  static int* flags[16] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (!flags[dev]) {
+    if (cudaMalloc(&flags[dev], sizeof(int)) != cudaSuccess) return flags[dev] = nullptr;
+    if (cudaMemsetAsync(flags[dev], 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess)
+      return nullptr;
+  }
+  return flags[dev];
+}
+
+lrep_status sliced_status(const char* what, cudaError_t e, void* stream) {
+  if (e != cudaSuccess) return cuda_fail(nullptr, what, e);
+  int h = 0;
+  int* f = sliced_err_flag(stream);
+  e = cudaMemcpyAsync(&h, f, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(nullptr, what, e);
+  if (h) {
+    g_err = std::string(what) + ": tensor-core pipeline wait expired";
+    return LREP_ERR_CUDA;
+  }
+  return LREP_OK;
+}
+
+lrep_status lrep_op_gram_sliced(int64_t n, int32_t a, int32_t b, const double* A, int64_t lda,
+                                const double* B, int64_t ldb, double* G, int64_t ldg,
+                                void* stream) {
+  if (n < 1 || a < 0 || b < 0 || (a > 0 && (!A || lda < n)) || (b > 0 && (!B || ldb < n)) ||
+      !G || ldg < a) {
+    g_err = "lrep_op_gram_sliced: invalid argument";
+    return LREP_ERR_ARG;
+  }
+  if (a == 0 || b == 0) return LREP_OK;
+  const size_t need = oz_gram_ws_bytes(n, a, b) / sizeof(double) + 64;
+  double* ws = nullptr;
+  lrep_status s = pool_take(need, &ws, stream);
+  if (s != LREP_OK) return s;
+  int* err = sliced_err_flag(stream);
+  if (!err) return cuda_fail(nullptr, "lrep_op_gram_sliced", cudaErrorMemoryAllocation);
+  cudaError_t e = oz_gram(n, seg1(A, lda, a), seg1(B, ldb, b), G, ldg, ws,
+                          need * sizeof(double), err, (cudaStream_t)stream);
+  return sliced_status("lrep_op_gram_sliced", e, stream);
+}
+
+lrep_status lrep_op_update_sliced(int64_t n, int32_t k, int32_t c, double alpha,
+                                  const double* A, int64_t lda, const double* B, int64_t ldb,
+                                  double beta, double* C, int64_t ldc, void* stream) {
+  if (n < 1 || k < 1 || k > 768 || c < 0 || !A || lda < n || !B || ldb < k || !C ||
+      ldc < n || beta == 0.0) {
+    g_err = "lrep_op_update_sliced: invalid argument (1 <= k <= 768, beta != 0)";
+    return LREP_ERR_ARG;
+  }
+  if (c == 0) return LREP_OK;
+  const size_t need = oz_update_ws_bytes(n, k, c) / sizeof(double) + 64;
+  double* ws = nullptr;
+  lrep_status s = pool_take(need, &ws, stream);
+  if (s != LREP_OK) return s;
+  int* err = sliced_err_flag(stream);
+  if (!err) return cuda_fail(nullptr, "lrep_op_update_sliced", cudaErrorMemoryAllocation);
+  cudaError_t e = oz_update(n, k, c, alpha, seg1(A, lda, k), B, ldb, beta, C, ldc, ws,
+                            need * sizeof(double), err, (cudaStream_t)stream);
+  return sliced_status("lrep_op_update_sliced", e, stream);
 }
 
 lrep_status lrep_op_update(int64_t n, int32_t k, int32_t c, double alpha, const double* A,

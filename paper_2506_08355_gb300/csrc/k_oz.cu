@@ -270,35 +270,72 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ C
   if (warp == 0) tmem_dealloc(tmem, G::TMEM_COLS);
 }
 
-// One CTA per column j of a column-major block (entries k = 0..n-1 of column
-// j contiguous, leading dimension lds): the exponent e with max_k |src_kj| <
-// 2^e (0 for a zero column) and the base-2^8 digits of src_kj / 2^e:
-// N = round(src_kj 2^(56 - e)) (|N| <= 2^56), written as balanced digits
-// N = sum_s d_s 2^(8 (7 - s)), d_2..d_7 in [-128, 127] and |d_1| <= 256,
-// stored as bf16 at dst[(s - 1) * sstride + j * ld + k].  Columns j >= ncols
-// and entries n <= k < ld are written as zeros, non-finite entries as NaN
-// digits.  Everything runs in integer arithmetic on the float64 bit pattern
-// (the FP64 pipe is the GPU's scarcest unit).
+// ---------------------------------------------------------------- slicing
+// A float64 x with scale exponent e (|x| < 2^e) becomes N = round(x 2^(56-e))
+// (|N| <= 2^56) written as balanced base-256 digits d_1..d_7
+// (N = sum_s d_s 2^(8 (7 - s)), d_2..d_7 in [-128, 127], |d_1| <= 256),
+// stored as bf16.  Integer arithmetic on the bit pattern only (the FP64
+// pipe is the GPU's scarcest unit); non-finite x gives NaN digits.
+constexpr uint64_t kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
+
 __device__ __forceinline__ uint16_t small_int_to_bf16(int d) {
   // |d| <= 256 has at most 8 significant bits: the upper half of the fp32
   // pattern is exact
   return (uint16_t)(__float_as_uint((float)d) >> 16);
 }
 
+// e with max < 2^e <= 2 max for the largest finite |entry| given by its bit
+// pattern (biased exponent E: e = E - 1022, a subnormal max counts as E = 1)
+__device__ __forceinline__ int scale_exponent(uint64_t maxbits) {
+  return maxbits ? max((int)(maxbits >> 52), 1) - 1022 : 0;
+}
+
+__device__ __forceinline__ void write_digits(uint64_t bits, int e, uint16_t* out,
+                                             int64_t sstride) {
+  const uint64_t a = bits & kAbs;
+  if (a >= kInf) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) out[(int64_t)s * sstride] = 0x7FC0;
+    return;
+  }
+  // |x| = mant 2^(E - 1075); N = round(|x| 2^(56 - e)) = round(mant 2^sh)
+  const int E = (int)(a >> 52);
+  const int64_t mant = (int64_t)(a & 0xFFFFFFFFFFFFFull) | (E ? (1ll << 52) : 0ll);
+  const int sh = max(E, 1) - 1075 + 56 - e;  // <= 3 since |x| < 2^e
+  int64_t N;
+  if (sh >= 0)
+    N = mant << sh;
+  else if (sh > -63)
+    N = (mant + (1ll << (-sh - 1))) >> (-sh);  // round half away from zero
+  else
+    N = 0;
+  if (bits >> 63) N = -N;
+  int d[S];
+#pragma unroll
+  for (int s = S - 1; s > 0; --s) {
+    d[s] = (int)(((N + 128) & 255) - 128);
+    N = (N - d[s]) >> 8;  // exact
+  }
+  d[0] = (int)N;
+#pragma unroll
+  for (int s = 0; s < S; ++s) out[(int64_t)s * sstride] = small_int_to_bf16(d[s]);
+}
+
+constexpr int kChunk = 8192;  // entries of one column per CTA
+
+// largest finite |entry| of each column of a segmented n x ncols block, as
+// bit patterns (atomicMax; maxbits zero on entry)
 __global__ void __launch_bounds__(256)
-oz_slice_kernel(int64_t n, int ncols, const double* __restrict__ src, int64_t lds,
-                uint16_t* __restrict__ dst, int64_t ld, int64_t sstride,
-                int* __restrict__ expo) {
-  constexpr uint64_t kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
-  const int j = blockIdx.x;
-  const bool live = j < ncols;
-  const uint64_t* col = (const uint64_t*)(src + (int64_t)j * lds);
-  uint64_t m = 0;  // largest finite |entry| (bit patterns of non-negative doubles order like them)
-  if (live)
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
-      const uint64_t a = col[k] & kAbs;
-      if (a < kInf && a > m) m = a;
-    }
+oz_colmax_kernel(Segs src, int64_t n, int ncols, unsigned long long* __restrict__ maxbits) {
+  const int j = blockIdx.y;
+  if (j >= ncols) return;
+  const uint64_t* col = (const uint64_t*)src.col(j);
+  const int64_t k0 = (int64_t)blockIdx.x * kChunk, k1 = min(n, k0 + kChunk);
+  uint64_t m = 0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const uint64_t a = col[k] & kAbs;
+    if (a < kInf && a > m) m = a;
+  }
   __shared__ uint64_t red[8];
   for (int o = 16; o > 0; o >>= 1) {
     const uint64_t t = __shfl_xor_sync(0xffffffffu, m, o);
@@ -306,57 +343,84 @@ oz_slice_kernel(int64_t n, int ncols, const double* __restrict__ src, int64_t ld
   }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
-  m = red[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
-  // e: max < 2^e <= 2 max (biased exponent field E of max: e = E - 1022;
-  // a subnormal max counts as E = 1)
-  int e = 0;
-  if (m > 0) e = max((int)(m >> 52), 1) - 1022;
-  if (threadIdx.x == 0 && expo) expo[j] = e;
-  uint16_t* out = dst + (int64_t)j * ld;
-  for (int64_t k = threadIdx.x; k < ld; k += blockDim.x) {
-    const uint64_t bits = (live && k < n) ? col[k] : 0ull;
-    const uint64_t a = bits & kAbs;
-    if (a >= kInf) {
-#pragma unroll
-      for (int s = 0; s < S; ++s) out[(int64_t)s * sstride + k] = 0x7FC0;
-      continue;
-    }
-    // |x| = mant 2^(E - 1075); N = round(|x| 2^(56 - e)) = round(mant 2^sh)
-    const int E = (int)(a >> 52);
-    const int64_t mant = (int64_t)(a & 0xFFFFFFFFFFFFFull) | (E ? (1ll << 52) : 0ll);
-    const int sh = max(E, 1) - 1075 + 56 - e;  // <= 3 since |x| < 2^e
-    int64_t N;
-    if (sh >= 0)
-      N = mant << sh;
-    else if (sh > -63)
-      N = (mant + (1ll << (-sh - 1))) >> (-sh);  // round half away from zero
-    else
-      N = 0;
-    if (bits >> 63) N = -N;
-    int d[S];
-#pragma unroll
-    for (int s = S - 1; s > 0; --s) {
-      d[s] = (int)(((N + 128) & 255) - 128);
-      N = (N - d[s]) >> 8;  // exact
-    }
-    d[0] = (int)N;
-#pragma unroll
-    for (int s = 0; s < S; ++s) out[(int64_t)s * sstride + k] = small_int_to_bf16(d[s]);
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+    if (m) atomicMax(&maxbits[j], (unsigned long long)m);
   }
 }
 
-__global__ void oz_reduce_kernel(int64_t n, int c, int C, int splits, int64_t rows_pad,
+// digit planes of the columns: plane s, column j, entry k at
+// dst[s * sstride + j * ld + k]; columns ncols..gridDim.y-1 and entries
+// n..ld-1 zero; expo[j] = the column's scale exponent
+__global__ void __launch_bounds__(256)
+oz_coldigits_kernel(Segs src, int64_t n, int ncols, int64_t ld,
+                    const unsigned long long* __restrict__ maxbits, uint16_t* __restrict__ dst,
+                    int64_t sstride, int* __restrict__ expo) {
+  const int j = blockIdx.y;
+  const bool live = j < ncols;
+  const int e = live ? scale_exponent(maxbits[j]) : 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && expo) expo[j] = e;
+  const uint64_t* col = live ? (const uint64_t*)src.col(j) : nullptr;
+  const int64_t k0 = (int64_t)blockIdx.x * kChunk, k1 = min(ld, k0 + kChunk);
+  uint16_t* out = dst + (int64_t)j * ld;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+    write_digits((live && k < n) ? col[k] : 0ull, e, out + k, sstride);
+}
+
+// Transposing slicer for a tall left operand: rows r of a segmented n x k
+// block become digit rows dst[s * sstride + r * ldk + kk] (per-row scale
+// expo[r]); rows n..gridDim.x*kRows-1 and entries k..ldk-1 zero.
+constexpr int kRows = 32;
+__global__ void __launch_bounds__(256)
+oz_rowslice_kernel(Segs src, int64_t n, int k, int64_t ldk, uint16_t* __restrict__ dst,
+                   int64_t sstride, int* __restrict__ expo) {
+  extern __shared__ uint64_t tile[];  // kRows x k, row-major
+  const int64_t r0 = (int64_t)blockIdx.x * kRows;
+  for (int e = threadIdx.x; e < kRows * k; e += blockDim.x) {
+    const int rr = e % kRows, kk = e / kRows;  // consecutive threads: consecutive rows
+    const int64_t r = r0 + rr;
+    tile[rr * k + kk] = (r < n) ? ((const uint64_t*)src.col(kk))[r] : 0ull;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ int rexp[kRows];
+  for (int rr = warp; rr < kRows; rr += (int)(blockDim.x >> 5)) {
+    uint64_t m = 0;
+    for (int kk = lane; kk < k; kk += 32) {
+      const uint64_t a = tile[rr * k + kk] & kAbs;
+      if (a < kInf && a > m) m = a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t t = __shfl_xor_sync(0xffffffffu, m, o);
+      m = t > m ? t : m;
+    }
+    if (lane == 0) {
+      rexp[rr] = scale_exponent(m);
+      if (expo) expo[r0 + rr] = rexp[rr];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kRows * ldk; e += blockDim.x) {
+    const int rr = (int)(e / ldk), kk = (int)(e % ldk);
+    write_digits(kk < k ? tile[rr * k + kk] : 0ull, rexp[rr],
+                 dst + (r0 + rr) * ldk + kk, sstride);
+  }
+}
+
+// Y[i, j] = alpha Y[i, j] + beta sum_z part[z][j][i] (fixed order; alpha = 0
+// does not read Y)
+__global__ void oz_reduce_kernel(int64_t nrows, int c, int C, int splits, int64_t rows_pad,
                                  const double* __restrict__ part, double* __restrict__ Y,
-                                 int64_t ldy, const int* __restrict__ skip) {
+                                 int64_t ldy, double alpha, double beta,
+                                 const int* __restrict__ skip) {
   if (skip && *skip) return;
-  const int64_t tot = n * c;
+  const int64_t tot = nrows * c;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / n, i = e % n;
+    const int64_t j = e / nrows, i = e % nrows;
     double s = 0.0;
     for (int z = 0; z < splits; ++z) s += part[((int64_t)z * C + j) * rows_pad + i];
-    Y[i + j * ldy] = s;
+    Y[i + j * ldy] = (alpha == 0.0) ? beta * s : fma(alpha, Y[i + j * ldy], beta * s);
   }
 }
 
@@ -382,47 +446,121 @@ bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, 
   return tc_make_map(map, base, inner, outer, ld, BK, box_outer);
 }
 
-template <int C>
-cudaError_t oz_group(const OzOperand& A, int c, const double* X, int64_t ldx, double* Y,
-                     int64_t ldy, uint8_t* ws, int* err, const int* skip, cudaStream_t st) {
-  using G = Cfg<C>;
-  const int64_t ldk = A.ldk, rp = A.rows_pad, n = A.n;
-  __nv_bfloat16* xs = (__nv_bfloat16*)ws;
-  int* tau = (int*)(ws + (size_t)S * C * ldk * 2);
-  double* part = (double*)(ws + (((size_t)S * C * ldk * 2 + 4 * 32 + 255) & ~(size_t)255));
-  oz_slice_kernel<<<C, 256, 0, st>>>(n, c, X, ldx, (uint16_t*)xs, ldk, (int64_t)C * ldk, tau);
+Segs segs_sub(const Segs& s, int j0, int cnt) {
+  Segs o{};
+  o.nseg = 0;
+  for (int q = 0; q < s.nseg && cnt > 0; ++q) {
+    if (j0 >= s.cols[q]) {
+      j0 -= s.cols[q];
+      continue;
+    }
+    const int take = std::min(cnt, s.cols[q] - j0);
+    o.ptr[o.nseg] = s.ptr[q] + (int64_t)j0 * s.ld[q];
+    o.ld[o.nseg] = s.ld[q];
+    o.cols[o.nseg] = take;
+    o.nseg++;
+    cnt -= take;
+    j0 = 0;
+  }
+  return o;
+}
+
+unsigned grid1(int64_t tot) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 8 * kNumSMs));
+}
+
+// digit planes of the c columns of X (k entries each, padded to ldk) for a
+// group of width C, into xs / tau (maxbits: C words of scratch)
+cudaError_t slice_columns(const Segs& X, int64_t k, int c, int C, int64_t ldk, uint16_t* xs,
+                          int* tau, unsigned long long* maxbits, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long) * C, st);
+  if (e != cudaSuccess) return e;
+  const unsigned chunks_n = (unsigned)std::max<int64_t>(1, (k + kChunk - 1) / kChunk);
+  const unsigned chunks_ld = (unsigned)std::max<int64_t>(1, (ldk + kChunk - 1) / kChunk);
+  oz_colmax_kernel<<<dim3(chunks_n, (unsigned)c), 256, 0, st>>>(X, k, c, maxbits);
   LREP_COUNT_LAUNCH();
-  cudaError_t e = cudaGetLastError();
+  oz_coldigits_kernel<<<dim3(chunks_ld, (unsigned)C), 256, 0, st>>>(X, k, c, ldk, maxbits, xs,
+                                                                    (int64_t)C * ldk, tau);
+  LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+// one column group: Y[:, 0:c] = alpha Y + beta A X for the sliced left
+// operand A (rows_pad x ldk planes behind mapA, row exponents sig) and the
+// c <= C columns of X
+template <int C>
+cudaError_t oz_group(const CUtensorMap& mapA, int64_t rows, int64_t rows_pad, int64_t ldk,
+                     const int* sig, const Segs& X, int64_t k, int c, double* Y, int64_t ldy,
+                     double alpha, double beta, uint8_t* ws, int* err, const int* skip,
+                     cudaStream_t st) {
+  using G = Cfg<C>;
+  uint16_t* xs = (uint16_t*)ws;
+  uint8_t* q = ws + (((size_t)S * C * ldk * 2 + 255) & ~(size_t)255);
+  int* tau = (int*)q;
+  unsigned long long* maxbits = (unsigned long long*)(q + 256);
+  double* part = (double*)(q + 1024);
+  cudaError_t e = slice_columns(X, k, c, C, ldk, xs, tau, maxbits, st);
   if (e != cudaSuccess) return e;
   CUtensorMap mx;
   if (!make_map(&mx, xs, ldk, (int64_t)S * C, ldk, S * C)) return cudaErrorInvalidValue;
-  const int64_t kt = ldk / BK, rt = rp / BM;
+  const int64_t kt = ldk / BK, rt = rows_pad / BM;
   const int per = oz_per(rt, kt, G::CTAS);
   const int splits = (int)((kt + per - 1) / per);
   static const cudaError_t attr = cudaFuncSetAttribute(
       oz_gemm_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
   if (attr != cudaSuccess) return attr;
   dim3 grid((unsigned)rt, (unsigned)splits);
-  oz_gemm_kernel<C><<<grid, G::THREADS, G::SMEM, st>>>(A.map, mx, (int)rp, per, (int)kt, A.sig, tau,
-                                                 part, err, skip);
+  oz_gemm_kernel<C><<<grid, G::THREADS, G::SMEM, st>>>(mapA, mx, (int)rows_pad, per, (int)kt,
+                                                       sig, tau, part, err, skip);
   LREP_COUNT_LAUNCH();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int64_t tot = n * c;
-  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 8 * kNumSMs));
-  oz_reduce_kernel<<<g, 256, 0, st>>>(n, c, C, splits, rp, part, Y, ldy, skip);
+  oz_reduce_kernel<<<grid1(rows * c), 256, 0, st>>>(rows, c, C, splits, rows_pad, part, Y, ldy,
+                                                    alpha, beta, skip);
   LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
-size_t group_ws_bytes(int64_t n, int C, int ctas) {
-  const int64_t ldk = oz_ldk(n), rp = oz_rows_pad(n);
+size_t group_ws_bytes(int64_t rows, int64_t k, int C, int ctas) {
+  const int64_t ldk = oz_ldk(k), rp = oz_rows_pad(rows);
   const int64_t kt = ldk / BK, rt = rp / BM;
   const int per = oz_per(rt, kt, ctas);
   const int64_t splits = (kt + per - 1) / per;
-  return (((size_t)S * C * ldk * 2 + 4 * 32 + 255) & ~(size_t)255) +
+  return (((size_t)S * C * ldk * 2 + 255) & ~(size_t)255) + 1024 +
          (size_t)splits * C * rp * sizeof(double) + 256;
 }
+
+size_t groups_ws_bytes(int64_t rows, int64_t k, int c) {
+  size_t b = group_ws_bytes(rows, k, 16, Cfg<16>::CTAS);
+  if (c > 16) b = std::max(b, group_ws_bytes(rows, k, 32, Cfg<32>::CTAS));
+  return b;
+}
+
+// all column groups of Y = alpha Y + beta A X
+cudaError_t oz_groups(const CUtensorMap& mapA, int64_t rows, int64_t rows_pad, int64_t ldk,
+                      const int* sig, const Segs& X, int64_t k, int c, double* Y, int64_t ldy,
+                      double alpha, double beta, uint8_t* ws, int* err, const int* skip,
+                      cudaStream_t st) {
+  for (int j0 = 0; j0 < c;) {
+    const int left = c - j0;
+    const Segs Xg = segs_sub(X, j0, std::min(left, 32));
+    cudaError_t e;
+    if (left <= 16) {
+      e = oz_group<16>(mapA, rows, rows_pad, ldk, sig, Xg, k, left, Y + (int64_t)j0 * ldy, ldy,
+                       alpha, beta, ws, err, skip, st);
+      j0 += left;
+    } else {
+      const int g = std::min(left, 32);
+      e = oz_group<32>(mapA, rows, rows_pad, ldk, sig, Xg, k, g, Y + (int64_t)j0 * ldy, ldy,
+                       alpha, beta, ws, err, skip, st);
+      j0 += g;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
@@ -430,7 +568,8 @@ int64_t oz_ldk(int64_t n) { return ((n + BK - 1) / BK) * BK; }
 int64_t oz_rows_pad(int64_t n) { return ((n + BM - 1) / BM) * BM; }
 
 size_t oz_operand_bytes(int64_t n) {
-  return (size_t)S * oz_rows_pad(n) * oz_ldk(n) * 2 + (size_t)oz_rows_pad(n) * sizeof(int) + 256;
+  return (size_t)S * oz_rows_pad(n) * oz_ldk(n) * 2 + (size_t)oz_rows_pad(n) * sizeof(int) +
+         (size_t)oz_rows_pad(n) * 8 + 512;
 }
 
 cudaError_t oz_slice_operator(int64_t n, const double* A, int64_t lda, OzOperand* o,
@@ -440,45 +579,88 @@ cudaError_t oz_slice_operator(int64_t n, const double* A, int64_t lda, OzOperand
   o->rows_pad = oz_rows_pad(n);
   const size_t planes = (size_t)S * o->rows_pad * o->ldk;
   o->sig = (int*)((uint8_t*)o->slices + planes * 2);
+  unsigned long long* maxbits =
+      (unsigned long long*)align256((size_t)(o->sig + o->rows_pad));
   // row i of the symmetric A is its column i
-  oz_slice_kernel<<<(unsigned)o->rows_pad, 256, 0, st>>>(
-      n, (int)n, A, lda, (uint16_t*)o->slices, o->ldk, o->rows_pad * o->ldk, o->sig);
-  LREP_COUNT_LAUNCH();
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = slice_columns(seg1(A, lda, (int)n), n, (int)n, (int)o->rows_pad, o->ldk,
+                                (uint16_t*)o->slices, o->sig, maxbits, st);
   if (e != cudaSuccess) return e;
   if (!make_map(&o->map, o->slices, o->ldk, (int64_t)S * o->rows_pad, o->ldk, BM))
     return cudaErrorInvalidValue;
   return cudaSuccess;
 }
 
-size_t oz_ws_bytes(int64_t n, int c) {
-  size_t b = group_ws_bytes(n, 16, Cfg<16>::CTAS);
-  if (c > 16) b = std::max(b, group_ws_bytes(n, 32, Cfg<32>::CTAS));
-  return b;
-}
+size_t oz_ws_bytes(int64_t n, int c) { return groups_ws_bytes(n, n, c); }
 
 cudaError_t oz_apply(const OzOperand& A, int c, const double* X, int64_t ldx, double* Y,
                      int64_t ldy, void* ws, size_t ws_bytes, int* err, const int* skip,
                      cudaStream_t st) {
   if (c <= 0) return cudaSuccess;
   if (ws_bytes < oz_ws_bytes(A.n, c)) return cudaErrorInvalidValue;
-  uint8_t* w = (uint8_t*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-  for (int j0 = 0; j0 < c;) {
-    const int left = c - j0;
-    cudaError_t e;
-    if (left <= 16) {
-      e = oz_group<16>(A, left, X + (int64_t)j0 * ldx, ldx, Y + (int64_t)j0 * ldy, ldy, w, err,
-                       skip, st);
-      j0 += left;
-    } else {
-      const int g = std::min(left, 32);
-      e = oz_group<32>(A, g, X + (int64_t)j0 * ldx, ldx, Y + (int64_t)j0 * ldy, ldy, w, err,
-                       skip, st);
-      j0 += g;
-    }
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  uint8_t* w = (uint8_t*)align256((size_t)ws);
+  return oz_groups(A.map, A.n, A.rows_pad, A.ldk, A.sig, seg1(X, ldx, c), A.n, c, Y, ldy, 0.0,
+                   1.0, w, err, skip, st);
+}
+
+// ------------------------------------------------ tall-skinny Gram / update
+size_t oz_gram_ws_bytes(int64_t n, int a, int b) {
+  const int64_t rp = oz_rows_pad(a), ldk = oz_ldk(n);
+  return align256((size_t)S * rp * ldk * 2) + align256((size_t)rp * 12) + 512 +
+         groups_ws_bytes(a, n, b);
+}
+
+cudaError_t oz_gram(int64_t n, const Segs& A, const Segs& B, double* G, int64_t ldg, void* ws,
+                    size_t ws_bytes, int* err, cudaStream_t st) {
+  const int a = A.total(), b = B.total();
+  if (a <= 0 || b <= 0) return cudaSuccess;
+  if (ws_bytes < oz_gram_ws_bytes(n, a, b)) return cudaErrorInvalidValue;
+  const int64_t rp = oz_rows_pad(a), ldk = oz_ldk(n);
+  uint8_t* w = (uint8_t*)align256((size_t)ws);
+  uint16_t* planes = (uint16_t*)w;
+  w += align256((size_t)S * rp * ldk * 2);
+  int* sig = (int*)w;
+  unsigned long long* maxbits = (unsigned long long*)(w + align256((size_t)rp * 4));
+  w += align256((size_t)rp * 12) + 512;
+  // rows of A^T = columns of A
+  cudaError_t e = slice_columns(A, n, a, (int)rp, ldk, planes, sig, maxbits, st);
+  if (e != cudaSuccess) return e;
+  CUtensorMap map;
+  if (!make_map(&map, planes, ldk, (int64_t)S * rp, ldk, BM)) return cudaErrorInvalidValue;
+  return oz_groups(map, a, rp, ldk, sig, B, n, b, G, ldg, 0.0, 1.0, w, err, nullptr, st);
+}
+
+size_t oz_update_ws_bytes(int64_t n, int k, int c) {
+  const int64_t rp = oz_rows_pad(n), ldk = oz_ldk(k);
+  return align256((size_t)S * rp * ldk * 2) + align256((size_t)rp * 4) + 512 +
+         groups_ws_bytes(n, k, c);
+}
+
+cudaError_t oz_update(int64_t n, int k, int c, double alpha, const Segs& A, const double* B,
+                      int64_t ldb, double beta, double* C, int64_t ldc, void* ws,
+                      size_t ws_bytes, int* err, cudaStream_t st) {
+  if (c <= 0 || n <= 0) return cudaSuccess;
+  if (k <= 0 || beta == 0.0) return cudaErrorInvalidValue;
+  if (ws_bytes < oz_update_ws_bytes(n, k, c)) return cudaErrorInvalidValue;
+  const int64_t rp = oz_rows_pad(n), ldk = oz_ldk(k);
+  uint8_t* w = (uint8_t*)align256((size_t)ws);
+  uint16_t* planes = (uint16_t*)w;
+  w += align256((size_t)S * rp * ldk * 2);
+  int* sig = (int*)w;
+  w += align256((size_t)rp * 4) + 512;
+  const size_t smem = (size_t)kRows * k * sizeof(uint64_t);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      oz_rowslice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (attr != cudaSuccess) return attr;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  oz_rowslice_kernel<<<(unsigned)(rp / kRows), 256, smem, st>>>(A, n, k, ldk, planes,
+                                                                rp * ldk, sig);
+  LREP_COUNT_LAUNCH();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap map;
+  if (!make_map(&map, planes, ldk, (int64_t)S * rp, ldk, BM)) return cudaErrorInvalidValue;
+  return oz_groups(map, n, rp, ldk, sig, seg1(B, ldb, c), k, c, C, ldc, alpha, beta, w, err,
+                   nullptr, st);
 }
 
 }  // namespace lrep

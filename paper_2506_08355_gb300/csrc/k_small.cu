@@ -79,8 +79,8 @@ __device__ bool chol_lower(double* L, int d, int* s_flag) {
 //  2. FP64 refinement of the right factor V by matrix products: two
 //     Newton-Schulz steps V <- V - V (V^T V - I)/2, then steps of
 //     simultaneous Jacobi rotations B = G V, C = B^T B, t_ab from the 2 x 2
-//     problem of columns (a, b), V <- V (I + T - T^T), each followed by one
-//     Newton-Schulz step, until max cos < d eps (quadratic convergence).
+//     problem of columns (a, b), V <- V (I + T - T^T), each followed by two
+//     Newton-Schulz steps, until max cos < d eps (quadratic convergence).
 // The column products of B keep each pair's rounding relative to
 // sigma_a sigma_b, so small singular values keep relative accuracy.
 // dyn: dynamic shared memory (dyn_bytes); matrices are column-major with
@@ -120,8 +120,10 @@ __device__ __forceinline__ double pair_rotation(double aa, double bb, double g) 
 // Simultaneous first-order rotations (V <- V (I + T - T^T)) are applied only
 // where |t| <= kRotCap; larger rotations (relative gap of the pair's singular
 // values below ~cos / kRotCap, e.g. a degenerate cluster) are done exactly,
-// one pair at a time, after the simultaneous steps.
-constexpr double kRotCap = 0.05;
+// one pair at a time, after the simultaneous steps.  A first-order step
+// leaves V non-orthogonal by O(t^2) <= 1e-6, which two Newton-Schulz steps
+// take below rounding (1e-6 -> ~1e-12 -> ~1e-24).
+constexpr double kRotCap = 1e-3;
 constexpr int kMaxPairs = 512;
 
 // Newton-Schulz step: V <- V - V (V^T V - I) / 2, using R and T as scratch.
@@ -335,6 +337,7 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
     mm_d(d, V, false, S, B, 1.0, 1.0);            // B = V + V Omega
     { double* t = V; V = B; B = t; }
     ns_step(d, V, B, S);
+    ns_step(d, V, B, S);
   }
   if (!converged) mm_d(d, G, false, V, B, 1.0, 0.0);
   // exact FP64 rotations of the nearly degenerate pairs (one warp, in order)
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(SMALL_T) small_lrep_one_kernel(SmallJob J, int
 // of V and the Ritz coefficients run as grid kernels (every d x d product
 // over ceil(d/16)^2 CTAs), so the FP64 work uses many SMs instead of one.
 // Same arithmetic as the one-CTA path: two Newton-Schulz steps, up to six
-// steps of simultaneous rotations (+ one Newton-Schulz step each), exact
+// steps of simultaneous rotations (+ two Newton-Schulz steps each), exact
 // sequential rotations of the nearly degenerate pairs, then X^, Y^.
 // Work layout (doubles, after L1, L2): G, V, T, R, B, S (d^2 each), then the
 // control block.
@@ -758,6 +761,7 @@ cudaError_t small_lrep_wide(const SmallJob& J, cudaStream_t st) {
     sq_check_kernel<<<1, 1, 0, st>>>(w.ctl, it, tol, it == 5); LREP_COUNT_LAUNCH();
     gemm(w.V, 0, w.R, w.T, 1.0, w.V, 1.0, 0.0, stop);       // T = V + V Omega
     copy(w.T, w.V, stop);
+    ns(stop);
     ns(stop);
   }
   gemm(w.G, 0, w.V, w.B, 1.0, nullptr, 0.0, 0.0, fail);     // B = G V

@@ -5,7 +5,8 @@
 //  * bit 1 (FP64_SLICED): seven bf16 digit planes for float64-accurate
 //    products by error-free slicing (k_oz.cu): every product that enters H^
 //    (eq. hat_H) and every residual (eq. tol), and the CG products when bit 0
-//    is clear.
+//    is clear; for any operator kind, the large tall-skinny Grams and block
+//    updates of the solver take the same route (bosp.cu).
 // Without bit 1, float64 products use the FP64 kernels.
 #include <cuda_runtime.h>
 
@@ -22,14 +23,17 @@ bool want_oz(const lrep_problem p) { return (p->opts.precision & LREP_PREC_FP64_
 
 bool split_ready(lrep_problem p) {
   const Operator& o = p->op;
-  return (!want_tc(p) || o.tcK) && (!want_oz(p) || o.ozK);
+  const bool dense = o.kind == OP_DENSE;
+  return (p->opts.precision == LREP_PREC_FP64 || o.tc_err) && (!want_tc(p) || o.tcK) &&
+         (!want_oz(p) || !dense || o.ozK);
 }
 
 size_t split_bytes(lrep_problem p) {
   const int64_t n = p->op.n;
   size_t b = 0;
   if (want_tc(p)) b += (size_t)2 * 2 * 2 * tc_ld(n) * n;  // K, M x (hi, lo) bf16
-  if (want_oz(p)) b += (size_t)2 * oz_operand_bytes(n);   // K, M x 7 digit planes
+  if (want_oz(p) && p->op.kind == OP_DENSE)
+    b += (size_t)2 * oz_operand_bytes(n);                 // K, M x 7 digit planes
   return b;
 }
 
@@ -37,8 +41,8 @@ lrep_status build_split(lrep_problem p) {
   Operator& o = p->op;
   free_split(p);
   if (p->opts.precision == LREP_PREC_FP64) return LREP_OK;
-  if (o.kind != OP_DENSE)
-    return p->fail(LREP_ERR_ARG, "tensor-core precisions need a dense operator");
+  if (want_tc(p) && o.kind != OP_DENSE)
+    return p->fail(LREP_ERR_ARG, "the bf16 hi/lo CG operator needs a dense operator");
   const int64_t n = o.n;
   const double* src[2] = {o.K, o.M};
   if (want_tc(p)) {
@@ -67,7 +71,7 @@ lrep_status build_split(lrep_problem p) {
       }
     }
   }
-  if (want_oz(p)) {
+  if (want_oz(p) && o.kind == OP_DENSE) {
     OzOperand* z[2] = {new OzOperand(), new OzOperand()};
     o.ozK = z[0];
     o.ozM = z[1];

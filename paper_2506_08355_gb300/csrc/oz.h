@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "common.cuh"
+
 namespace lrep {
 
 constexpr int kOzSlices = 7;  // base-2^8 digits per float64 value
@@ -37,5 +39,19 @@ size_t oz_ws_bytes(int64_t n, int c);
 cudaError_t oz_apply(const OzOperand& A, int c, const double* X, int64_t ldx, double* Y,
                      int64_t ldy, void* ws, size_t ws_bytes, int* err, const int* skip,
                      cudaStream_t st);
+
+// Tall-skinny products with float64 accuracy on the same machinery (same
+// error bound form, with e_i bounding row i of the left factor and f_j
+// column j of the right factor):
+//   G (a x b, ldg) = A^T B for segmented n x a and n x b blocks;
+//   C (n x c, ldc) = alpha C + beta A B for a segmented n x k block A and a
+//   k x c matrix B (ldb); beta != 0.
+size_t oz_gram_ws_bytes(int64_t n, int a, int b);
+cudaError_t oz_gram(int64_t n, const Segs& A, const Segs& B, double* G, int64_t ldg, void* ws,
+                    size_t ws_bytes, int* err, cudaStream_t st);
+size_t oz_update_ws_bytes(int64_t n, int k, int c);
+cudaError_t oz_update(int64_t n, int k, int c, double alpha, const Segs& A, const double* B,
+                      int64_t ldb, double beta, double* C, int64_t ldc, void* ws,
+                      size_t ws_bytes, int* err, cudaStream_t st);
 
 }  // namespace lrep

@@ -71,6 +71,12 @@ EXPORTS = {
     "lrep_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32]),
     "lrep_server_destroy": (C.c_int, [C.c_void_p]),
     "lrep_server_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lrep_op_gram_sliced": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                      C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                      C.c_void_p]),
+    "lrep_op_update_sliced": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_double,
+                                        C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                        C.c_double, C.c_void_p, C.c_int64, C.c_void_p]),
     "lrep_op_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
                                 C.c_void_p, C.c_int64]),
     "lrep_op_apply_cg": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
@@ -392,19 +398,22 @@ def _st(stream):
     return _stream(stream)
 
 
-def gram(A, B, G, stream=None):
-    """G (b, a) tensor <- A^T B for device blocks A (a, n), B (b, n)."""
+def gram(A, B, G, stream=None, sliced=False):
+    """G (b, a) tensor <- A^T B for device blocks A (a, n), B (b, n);
+    sliced: float64 accuracy on the tensor cores (lrep_op_gram_sliced)."""
     n = A.shape[1]
-    _check(lib().lrep_op_gram(n, A.shape[0], B.shape[0], _ptr(A), _ld(A), _ptr(B),
-                              _ld(B), _ptr(G), _ld(G), _st(stream)))
+    f = lib().lrep_op_gram_sliced if sliced else lib().lrep_op_gram
+    _check(f(n, A.shape[0], B.shape[0], _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(G), _ld(G),
+             _st(stream)))
 
 
-def update(A, B, Cm, alpha, beta, stream=None):
-    """Cm <- alpha Cm + beta A B for device A (k, n), B (c, k), Cm (c, n)."""
+def update(A, B, Cm, alpha, beta, stream=None, sliced=False):
+    """Cm <- alpha Cm + beta A B for device A (k, n), B (c, k), Cm (c, n);
+    sliced: float64 accuracy on the tensor cores (lrep_op_update_sliced)."""
     n = A.shape[1]
-    _check(lib().lrep_op_update(n, A.shape[0], Cm.shape[0], alpha, _ptr(A), _ld(A),
-                                _ptr(B), _ld(B), beta, _ptr(Cm), _ld(Cm),
-                                _st(stream)))
+    f = lib().lrep_op_update_sliced if sliced else lib().lrep_op_update
+    _check(f(n, A.shape[0], Cm.shape[0], alpha, _ptr(A), _ld(A), _ptr(B), _ld(B), beta,
+             _ptr(Cm), _ld(Cm), _st(stream)))
 
 
 def small_lrep(Kh, Mh, lam, Xh, Yh, stream=None):

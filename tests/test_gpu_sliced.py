@@ -140,3 +140,100 @@ def test_sliced_solver_full_size_dense(L, prec):
     assert prob.solve(64, 16, 1e-10) == L.OK
     check(R.DenseOp(p["K"], p["M"]), prob, g, 1e-10, 64)
     prob.close()
+
+
+# ---------------------------------------------- tall-skinny Gram and update
+
+
+def _colscale(M):
+    return np.array([math.frexp(v)[1] if v > 0 else 0 for v in np.abs(M).max(axis=0)])
+
+
+@pytest.mark.parametrize("n,a,b", [(70001, 40, 33), (5000, 130, 70), (300, 5, 1)])
+def test_sliced_gram_error_bound(L, n, a, b):
+    """G = A^T B: ragged n (many k-tiles and splits), two row tiles, three
+    column groups; entries over ~20 binades."""
+    import torch
+    rng = np.random.default_rng(n + a + b)
+    A = rng.standard_normal((n, a)) * np.exp(rng.uniform(-7, 7, (n, a)))
+    B = rng.standard_normal((n, b)) * np.exp(rng.uniform(-7, 7, (n, b)))
+    Ad = torch.tensor(np.ascontiguousarray(A.T), device="cuda")
+    Bd = torch.tensor(np.ascontiguousarray(B.T), device="cuda")
+    Gd = torch.full((b, a), np.nan, dtype=torch.float64, device="cuda")
+    L.gram(Ad, Bd, Gd, sliced=True)
+    torch.cuda.synchronize()
+    G = Gd.cpu().numpy().T
+    assert np.all(np.isfinite(G))
+    ea, eb = _colscale(A), _colscale(B)
+    worst = 0.0
+    for i in rng.choice(a, min(a, 10), replace=False):
+        for j in rng.choice(b, min(b, 6), replace=False):
+            scale = n * U * 2.0 ** (ea[i] + eb[j])
+            worst = max(worst, _err(G[i, j], _exact_dot(A[:, i], B[:, j])) / scale)
+    assert worst <= 1.0 / 8, worst
+
+
+def test_sliced_gram_and_update_exact_on_short_mantissas(L):
+    import torch
+    rng = np.random.default_rng(77)
+    n, a, k, c = 3001, 37, 97, 45
+    A = rng.integers(-2048, 2049, (n, a)).astype(np.float64) * 2.0 ** -6
+    B = rng.integers(-512, 513, (n, a)).astype(np.float64)
+    Gd = torch.zeros((a, a), dtype=torch.float64, device="cuda")
+    L.gram(torch.tensor(A.T.copy(), device="cuda"), torch.tensor(B.T.copy(), device="cuda"),
+           Gd, sliced=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Gd.cpu().numpy().T, A.T @ B)
+    T = rng.integers(-1000, 1001, (n, k)).astype(np.float64) * 2.0 ** -4
+    W = rng.integers(-300, 301, (k, c)).astype(np.float64)
+    C0 = rng.integers(-100, 101, (n, c)).astype(np.float64)
+    Cd = torch.tensor(C0.T.copy(), device="cuda")
+    L.update(torch.tensor(T.T.copy(), device="cuda"), torch.tensor(W.T.copy(), device="cuda"),
+             Cd, 0.5, -2.0, sliced=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Cd.cpu().numpy().T, 0.5 * C0 - 2.0 * (T @ W))
+
+
+@pytest.mark.parametrize("n,k,c", [(5000, 97, 45), (20000, 384, 32), (129, 1, 3)])
+def test_sliced_update_error_bound(L, n, k, c):
+    """C = alpha C + beta A B with per-row scales of the tall A."""
+    import torch
+    rng = np.random.default_rng(n + k + c)
+    A = rng.standard_normal((n, k)) * np.exp(rng.uniform(-7, 7, (n, 1)) + rng.uniform(-3, 3, (n, k)))
+    B = rng.standard_normal((k, c)) * np.exp(rng.uniform(-5, 5, (k, c)))
+    C0 = rng.standard_normal((n, c))
+    alpha, beta = 0.75, -1.25
+    Cd = torch.tensor(C0.T.copy(), device="cuda")
+    L.update(torch.tensor(A.T.copy(), device="cuda"), torch.tensor(B.T.copy(), device="cuda"),
+             Cd, alpha, beta, sliced=True)
+    torch.cuda.synchronize()
+    Cg = Cd.cpu().numpy().T
+    ra = np.array([math.frexp(v)[1] if v > 0 else 0 for v in np.abs(A).max(axis=1)])
+    fb = _colscale(B)
+    worst = 0.0
+    for i in rng.choice(n, min(n, 12), replace=False):
+        for j in rng.choice(c, min(c, 6), replace=False):
+            num, den = _exact_dot(A[i], B[:, j])
+            exact = alpha * C0[i, j] + beta * (num / den)
+            # rounding of the last fma against the exact float64 combination
+            bound = abs(beta) * k * U * 2.0 ** (ra[i] + fb[j]) / 8 + 4 * U * (abs(exact) + abs(alpha * C0[i, j]))
+            worst = max(worst, abs(Cg[i, j] - exact) / bound)
+    assert worst <= 1.0, worst
+
+
+def test_sliced_tall_skinny_full_size_stencil(L):
+    """The 64^3 BdG-like stencil workload with precision FP64_SLICED: the
+    stencil products stay FP64, the Grams and block updates run sliced on the
+    tensor cores; same eigenvalues as the oracle's stored literal Alg. 2 run,
+    residuals and biorthogonality re-checked on the CPU."""
+    from test_gpu_solver import _stored_run
+    lam_ref, _ = _stored_run("config2_oracle_run.txt")
+    p = synth.config(2)
+    op = R.StencilOp(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"], p["dM"])
+    prob = L.Problem.stencil(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"], p["dM"])
+    prob.set_nullspace(p["X0"])
+    prob.set_options(precision=L.PREC_FP64_SLICED)
+    assert prob.solve(32, 16, 1e-10) == L.OK
+    lam, X, Y = check(op, prob, lam_ref, 1e-10, 32, rtol=1e-10)
+    assert np.abs(p["X0"][:, 0] @ Y).max() < 1e-9
+    prob.close()
