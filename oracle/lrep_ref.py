@@ -63,14 +63,18 @@ import numpy as np
 
 
 class DenseOp:
-    """K, M stored as dense symmetric matrices."""
+    """K, M (and optionally the SPD B of the generalized LREP, Remark on
+    the generalized LREP) stored as dense symmetric matrices."""
 
-    def __init__(self, K, M):
+    def __init__(self, K, M, B=None):
         self.K = np.asarray(K, dtype=np.float64)
         self.M = np.asarray(M, dtype=np.float64)
+        self.B = None if B is None else np.asarray(B, dtype=np.float64)
         self.n = self.K.shape[0]
 
     def apply(self, which, X):
+        if which == "B":
+            return X if self.B is None else self.B @ X
         return (self.K if which == "K" else self.M) @ X
 
 
@@ -206,7 +210,7 @@ def fix_sign(X, Y):
 # Alg. 1 and its classical variant
 
 
-def mgs_biorth(X, Y, tau=1e-10, ref_norms=None):
+def mgs_biorth(X, Y, tau=1e-10, ref_norms=None, Bf=None):
     """Alg. 1 (MGS-Biorth) with the discard rule of the Remark after it.
 
     For l = 1..m: p = x_l, q = y_l; for each kept j < l:
@@ -215,23 +219,28 @@ def mgs_biorth(X, Y, tau=1e-10, ref_norms=None):
     p_l = p / r_ll, q_l = q / s_ll.  Pairs with |eta| <= tau ||x_l|| ||y_l||
     (or non-finite eta) are dropped; ``ref_norms`` = (||x_l||, ||y_l||)
     arrays replace the input norms when the inputs were projected before.
+    ``Bf``: the B-inner product <u, v>_B = u^T B v of the generalized LREP
+    (Remark on the generalized LREP), given as v -> B v; norms are then
+    B-norms.
     Returns (P, Q, kept indices).
     Parity: pinned (Table 1 losses, P^T Q = I, span checks, LU identity).
     """
     X = np.asarray(X, dtype=np.float64)
     Y = np.asarray(Y, dtype=np.float64)
+    Bf = (lambda v: v) if Bf is None else Bf
     if ref_norms is None:
-        ref_norms = (np.linalg.norm(X, axis=0), np.linalg.norm(Y, axis=0))
+        ref_norms = (np.sqrt(np.abs(np.sum(X * Bf(X), axis=0))),
+                     np.sqrt(np.abs(np.sum(Y * Bf(Y), axis=0))))
     P, Q, kept = [], [], []
     for l in range(X.shape[1]):
         p = X[:, l].copy()
         q = Y[:, l].copy()
         for pj, qj in zip(P, Q):
-            r = qj @ p
+            r = qj @ Bf(p)
             p -= r * pj
-            s = pj @ q
+            s = pj @ Bf(q)
             q -= s * qj
-        eta = p @ q
+        eta = p @ Bf(q)
         bound = tau * ref_norms[0][l] * ref_norms[1][l]
         if not np.isfinite(eta) or abs(eta) <= bound or eta == 0.0:
             continue
@@ -329,14 +338,18 @@ def cg(apply_fn, B, tol, maxit):
     return X, it
 
 
-def residuals(op, X, Y, lam, KX=None, MY=None):
-    """eq. tol: ||H xi - lam xi|| / ((1 + lam) ||xi||), xi = [y; x].
+def residuals(op, X, Y, lam, KX=None, MY=None, BX=None, BY=None):
+    """eq. tol: ||H xi - lam xi|| / ((1 + lam) ||xi||), xi = [y; x]; for the
+    generalized LREP H xi - lam diag(B, B) xi.
 
-    KX, MY may be passed when already formed (K U X^ = (K U) X^)."""
+    KX, MY (BX, BY) may be passed when already formed (K U X^ = (K U) X^)."""
     KX = op.apply("K", X) if KX is None else KX
     MY = op.apply("M", Y) if MY is None else MY
-    R1 = KX - Y * lam[None, :]
-    R2 = MY - X * lam[None, :]
+    gen = getattr(op, "B", None) is not None
+    BX = (op.apply("B", X) if gen else X) if BX is None else BX
+    BY = (op.apply("B", Y) if gen else Y) if BY is None else BY
+    R1 = KX - BY * lam[None, :]
+    R2 = MY - BX * lam[None, :]
     num = np.sqrt(np.sum(R1 * R1, axis=0) + np.sum(R2 * R2, axis=0))
     den = (1.0 + lam) * np.sqrt(np.sum(X * X, axis=0) + np.sum(Y * Y, axis=0))
     return num / den
@@ -360,16 +373,18 @@ def setup_nullspace(op, X0, Y0=None, cg_tol=1e-14, cg_maxit=50000):
     Y0 solves M Y0 = X0 (Remark "numerical computation of generalized
     nullspace": CG on the SPD system) unless given; then with
     X0^T Y0 = C^T C (Cholesky), X0 <- X0 C^-1, Y0 <- Y0 C^-1 (eq. V0_basis)
-    so that X0^T Y0 = I.
+    so that X0^T Y0 = I.  Generalized LREP: M Y0 = B X0 and X0^T B Y0 = I.
     """
     X0 = np.asarray(X0, dtype=np.float64).reshape(op.n, -1)
+    gen = getattr(op, "B", None) is not None
+    BX0 = op.apply("B", X0) if gen else X0
     if Y0 is None:
         if isinstance(op, DenseOp):
-            Y0 = np.linalg.solve(op.M, X0)
+            Y0 = np.linalg.solve(op.M, BX0)
         else:
-            Y0, _ = cg(lambda Z: op.apply("M", Z), X0, cg_tol, cg_maxit)
+            Y0, _ = cg(lambda Z: op.apply("M", Z), BX0, cg_tol, cg_maxit)
     Y0 = np.asarray(Y0, dtype=np.float64).reshape(op.n, -1)
-    C = np.linalg.cholesky(X0.T @ Y0).T
+    C = np.linalg.cholesky(BX0.T @ Y0).T
     X0 = np.linalg.solve(C.T, X0.T).T
     Y0 = np.linalg.solve(C.T, Y0.T).T
     return X0, Y0
@@ -403,6 +418,10 @@ def bosp(op, nev, block, tol, X0=None, Y0=None, start=None, s=3, ngs=1,
     w = min(s * nb if moving else nev, n - r)
     Kf = lambda Z: op.apply("K", Z)
     Mf = lambda Z: op.apply("M", Z)
+    # generalized LREP (Remark on the generalized LREP): every
+    # biorthogonality is in the B-inner product u^T B v
+    gen = getattr(op, "B", None) is not None
+    Bf = (lambda Z: op.apply("B", Z)) if gen else (lambda Z: Z)
     matvecs = 0
     if r:
         X0, Y0 = setup_nullspace(op, X0, Y0)
@@ -421,9 +440,9 @@ def bosp(op, nev, block, tol, X0=None, Y0=None, start=None, s=3, ngs=1,
         U = np.array(start[0][:, :d0], dtype=np.float64)
         V = np.array(start[1][:, :d0], dtype=np.float64)
     # Step 2: U = (I - X0 Y0^T) U, V = (I - Y0 X0^T) V, then Alg. 1
-    U = U - Dx @ (Dy.T @ U)
-    V = V - Dy @ (Dx.T @ V)
-    U, V, _ = mgs_biorth(U, V, discard_tol)
+    U = U - Dx @ (Dy.T @ Bf(U))
+    V = V - Dy @ (Dx.T @ Bf(V))
+    U, V, _ = mgs_biorth(U, V, discard_tol, Bf=Bf)
     w_prev = min(w, U.shape[1])
     locked_lam = []
     history = []
@@ -435,8 +454,8 @@ def bosp(op, nev, block, tol, X0=None, Y0=None, start=None, s=3, ngs=1,
         it += 1
         d = U.shape[1]
         # safeguard: restore U^T V = I (see module readings)
-        if np.abs(U.T @ V - np.eye(d)).max() > rebiorth_tol:
-            U, V, _ = mgs_biorth(U, V, discard_tol)
+        if np.abs(U.T @ Bf(V) - np.eye(d)).max() > rebiorth_tol:
+            U, V, _ = mgs_biorth(U, V, discard_tol, Bf=Bf)
             d = U.shape[1]
             rebiorths += 1
         # Step 3: H^ (eq. hat_H), small LREP, pullback (eq. eigenVector-pullback)
@@ -454,7 +473,8 @@ def bosp(op, nev, block, tol, X0=None, Y0=None, start=None, s=3, ngs=1,
         Xt = U @ Xh[:, :wv]
         Yt = V @ Yh[:, :wv]
         # Step 4: residuals (eq. tol); K X~ = (K U) X^, M Y~ = (M V) Y^
-        eps = residuals(op, Xt, Yt, lam[:wv], KU @ Xh[:, :wv], MV @ Yh[:, :wv])
+        eps = residuals(op, Xt, Yt, lam[:wv], KU @ Xh[:, :wv], MV @ Yh[:, :wv],
+                        Bf(Xt), Bf(Yt))
         history.append(eps.copy())
         c = 0
         while c < wv and eps[c] < tol:
@@ -476,7 +496,8 @@ def bosp(op, nev, block, tol, X0=None, Y0=None, start=None, s=3, ngs=1,
             sl = slice(win0, win0 + wv)
             Xt = U @ Xh[:, sl]
             Yt = V @ Yh[:, sl]
-            eps = residuals(op, Xt, Yt, lam[sl], KU @ Xh[:, sl], MV @ Yh[:, sl])
+            eps = residuals(op, Xt, Yt, lam[sl], KU @ Xh[:, sl], MV @ Yh[:, sl],
+                            Bf(Xt), Bf(Yt))
         end = win0 + wv
         active = [win0 + i for i in range(wv) if not eps[i] < tol][:nb]
         # Step 5: eq. hat_pq, small biorth, P~ = U P^, Q~ = V Q^
@@ -492,7 +513,7 @@ def bosp(op, nev, block, tol, X0=None, Y0=None, start=None, s=3, ngs=1,
         if win0 > 0:
             Ph, Qh = Ph[:, :0], Qh[:, :0]   # P^ = 0 after a move
             pq_ref = (pq_ref[0][:0], pq_ref[1][:0])
-        Ph, Qh, _ = mgs_biorth(Ph, Qh, discard_tol, pq_ref)
+        Ph, Qh, _ = mgs_biorth(Ph, Qh, discard_tol, pq_ref)  # in R^d: U^T B V = I
         Pt = U @ Ph
         Qt = V @ Qh
         # Step 6: eq. block_GS with CG, then eq. update_W / update_Z
@@ -502,20 +523,22 @@ def bosp(op, nev, block, tol, X0=None, Y0=None, start=None, s=3, ngs=1,
         KXb = KU @ Xh[:, active]
         MYb = MV @ Yh[:, active]
         Wj = np.zeros_like(Xb)
+        BXb, BYb = Bf(Xb), Bf(Yb)
         for _ in range(ngs):
-            rhs = Wj * lam_b[None, :] + (Xb * lam_b[None, :] - MYb)
+            rhs = Bf(Wj) * lam_b[None, :] + (BXb * lam_b[None, :] - MYb)
             Zj, k1 = cg(Mf, rhs, cg_tol, cg_maxit)
-            rhs = Zj * lam_b[None, :] + (Yb * lam_b[None, :] - KXb)
+            rhs = Bf(Zj) * lam_b[None, :] + (BYb * lam_b[None, :] - KXb)
             if Q0 is not None:
                 rhs = rhs - Q0 @ (Q0.T @ rhs)
             Wj, k2 = cg(Kf, rhs, cg_tol, cg_maxit)
             matvecs += (k1 + k2) * len(active)
         A = np.hstack([Dx, Xt, Pt])
         B = np.hstack([Dy, Yt, Qt])
-        Wt = Wj - A @ (B.T @ Wj)
-        Zt = Zj - B @ (A.T @ Zj)
-        wz_ref = (np.linalg.norm(Wj, axis=0), np.linalg.norm(Zj, axis=0))
-        Wt, Zt, _ = mgs_biorth(Wt, Zt, discard_tol, wz_ref)
+        Wt = Wj - A @ (B.T @ Bf(Wj))
+        Zt = Zj - B @ (A.T @ Bf(Zj))
+        wz_ref = (np.sqrt(np.abs(np.sum(Wj * Bf(Wj), axis=0))),
+                  np.sqrt(np.abs(np.sum(Zj * Bf(Zj), axis=0))))
+        Wt, Zt, _ = mgs_biorth(Wt, Zt, discard_tol, wz_ref, Bf=Bf)
         # Step 7
         U = np.hstack([Xt, Pt, Wt])
         V = np.hstack([Yt, Qt, Zt])

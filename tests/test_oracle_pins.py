@@ -458,3 +458,29 @@ def test_generalized_definition_pins():
     np.testing.assert_allclose(K @ Xg, Bm @ Yg * lg, atol=1e-9)
     np.testing.assert_allclose(M @ Yg, Bm @ Xg * lg, atol=1e-9)
     np.testing.assert_allclose(Xg.T @ Bm @ Yg, np.eye(nev), atol=1e-10)
+
+
+def test_bosp_generalized_vs_definition():
+    """Alg. 2 in the B-inner product (Remark on the generalized LREP)
+    against the definition route through B = L L^T: simple window, moving
+    window, and a singular K deflated through V0 (M Y0 = B X0)."""
+    rng = np.random.default_rng(31)
+    for n, nev, nb, r in ((120, 4, 4, 0), (300, 12, 4, 0), (200, 6, 3, 2)):
+        Q1, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        Q2, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        k = rng.uniform(0.5, 10, n)
+        k[:r] = 0.0
+        K = (Q1 * k) @ Q1.T
+        M = (Q2 * rng.uniform(0.5, 10, n)) @ Q2.T
+        Q3, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        Bm = (Q3 * rng.uniform(0.5, 2.0, n)) @ Q3.T
+        op = R.DenseOp(K, M, Bm)
+        lam_d, Xd, Yd = R.lrep_definition_gen(K, M, Bm, nev, r)
+        res = R.bosp(op, nev, nb, 1e-10, X0=Q1[:, :r] if r else None)
+        assert res.converged and res.nconv == nev
+        np.testing.assert_allclose(res.lam, lam_d, rtol=1e-10)
+        assert R.residuals(op, res.X, res.Y, res.lam).max() < 1e-10
+        np.testing.assert_allclose(res.X.T @ Bm @ res.Y, np.eye(nev), atol=1e-10)
+        np.testing.assert_allclose(np.abs(res.X), np.abs(Xd), atol=1e-6)
+        if r:
+            assert np.abs(Q1[:, :r].T @ Bm @ res.Y).max() < 1e-9
