@@ -59,7 +59,10 @@ enum { LREP_MEM_HOST = 0, LREP_MEM_DEVICE_COPY = 1, LREP_MEM_DEVICE_BORROW = 2 }
 /* LREP_FORM_AB: inputs are A and B (K = A - B, M = A + B, eq. xy_algebra);
  * LREP_FORM_KM: inputs are K and M directly. */
 enum { LREP_FORM_AB = 0, LREP_FORM_KM = 1 };
-enum { LREP_OP_K = 0, LREP_OP_M = 1 };
+/* LREP_OP_B: the SPD mass matrix B of the generalized LREP (set by
+ * lrep_set_mass_*; a callback operator is asked for it when
+ * lrep_set_mass_callback was called). */
+enum { LREP_OP_K = 0, LREP_OP_M = 1, LREP_OP_B = 2 };
 /* Arithmetic of the float64-accurate work and of the CG products (two
  * independent bits; bit 0 needs a dense operator).
  * FP64: every product in float64 (FP64 FMA units).
@@ -174,6 +177,23 @@ lrep_status lrep_find_nullspace(lrep_problem p, int32_t r_max, double tol,
                                 int32_t maxit, double* X0_out, int64_t ld_out,
                                 int32_t mem_out, int32_t* r_host,
                                 int32_t* iters_host);
+
+/* Generalized LREP (Remark on the generalized LREP):
+ *   [[0, K], [M, 0]] [y; x] = lam [[B, 0], [0, B]] [y; x],
+ * i.e. K x = lam B y, M y = lam B x, with B symmetric positive definite.
+ * The solve then runs Alg. 2 in the B-inner product <u, v>_B = u^T B v:
+ * X^T B Y = I, residuals of eq. tol with B Y, B X in the lam terms, the
+ * block Gauss-Seidel right-hand sides B X~ Lam - M Y~ and B Y~ Lam - K X~,
+ * the projections of eq. update_W/Z and Alg. 1 in the B-inner product, and
+ * M Y0 = B X0 with X0^T B Y0 = I for the nullspace.
+ * Dense problems: B n x n column-major (ld >= n; mem as for
+ * lrep_create_dense).  CSR problems: B as CSR arrays (rowptr int64[n+1],
+ * colind int32[nnz], values float64[nnz]).  Callback problems: the callback
+ * is called with op = LREP_OP_B.  B = NULL (dense, CSR) clears it. */
+lrep_status lrep_set_mass_dense(lrep_problem p, const double* B, int64_t ld, int32_t mem);
+lrep_status lrep_set_mass_csr(lrep_problem p, const int64_t* rowptr,
+                              const int32_t* colind, const double* values, int32_t mem);
+lrep_status lrep_set_mass_callback(lrep_problem p, int32_t enable);
 
 lrep_status lrep_set_options(lrep_problem p, const lrep_options* opts);
 

@@ -56,20 +56,25 @@ lrep_status apply_op(lrep_problem p, int which, int c, const double* X,
   Operator& o = p->op;
   cudaError_t e = cudaSuccess;
   const bool isK = (which == LREP_OP_K);
+  const bool isB = (which == LREP_OP_B);
+  if (isB && !o.hasB) return p->fail(LREP_ERR_STATE, "no mass matrix B set");
   switch (o.kind) {
     case OP_DENSE:
       if (p->opts.precision & LREP_PREC_FP64_SLICED) {
-        if (!o.ozK) return p->fail(LREP_ERR_STATE, "digit planes of the operator missing");
+        if (!o.ozK || (isB && !o.ozB))
+          return p->fail(LREP_ERR_STATE, "digit planes of the operator missing");
         return apply_sliced(p, which, c, X, ldx, Y, ldy, skip, ws, ws_elems);
       }
-      e = dense_apply_f64(o.n, c, isK ? o.K : o.M, o.ld, X, ldx, Y, ldy, ws,
+      e = dense_apply_f64(o.n, c, isB ? o.B : isK ? o.K : o.M, o.ld, X, ldx, Y, ldy, ws,
                           ws_elems, skip, p->stream);
       break;
     case OP_CSR:
-      e = csr_apply_f64(o.n, isK ? o.rpK : o.rpM, isK ? o.ciK : o.ciM,
-                        isK ? o.vK : o.vM, c, X, ldx, Y, ldy, skip, p->stream);
+      e = csr_apply_f64(o.n, isB ? o.rpB : isK ? o.rpK : o.rpM,
+                        isB ? o.ciB : isK ? o.ciK : o.ciM, isB ? o.vB : isK ? o.vK : o.vM,
+                        c, X, ldx, Y, ldy, skip, p->stream);
       break;
     case OP_STENCIL:
+      if (isB) return p->fail(LREP_ERR_STATE, "stencil problems have no mass matrix");
       e = stencil_apply_f64(o.nx, o.ny, o.nz, o.coef_h2, isK ? o.dK : o.dM, c,
                             X, ldx, Y, ldy, skip, p->stream);
       break;
@@ -96,6 +101,11 @@ lrep_status apply_op(lrep_problem p, int which, int c, const double* X,
 }
 
 namespace {
+
+__global__ void diag_copy_kernel(int m, const double* __restrict__ G, int ldg,
+                                 double* __restrict__ out) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) out[i] = G[i + (size_t)i * ldg];
+}
 
 #define LCK(expr)                                                                   \
   do {                                                                              \
@@ -126,6 +136,12 @@ struct Solver {
   int d = 0;
   // deflation basis [X0 | locked], [Y0 | locked]; orthonormal basis of X0
   double *Dx, *Dy, *Q0;
+  // generalized LREP (mass matrix B): B-companions of the bases, carried by
+  // the same combinations (B U, B V, B Dx, B Dy) and fresh B W, B Z
+  bool gen = false;
+  double* BU[2];
+  double* BV[2];
+  double *BDx, *BDy, *BWr, *BZr, *BT, *BTW, *BTZ;
   // CG and W/Z blocks
   double *Rhs, *Zr, *Wr, *Rr, *Pr, *Qr, *TW, *TZ;
   // small matrices
@@ -202,6 +218,13 @@ struct Solver {
   double* KUcur() { return KX[cur] + off * ld; }
   double* MVcur() { return MY[cur] + off * ld; }
   int nx() const { return 1 - cur; }
+  // B-companion of a basis block (the block itself when B = I)
+  double* BUcur() { return gen ? BU[cur] + off * ld : Ucur(); }
+  double* BVcur() { return gen ? BV[cur] + off * ld : Vcur(); }
+  double* bux(int t) { return gen ? BU[t] : UX[t]; }
+  double* bvy(int t) { return gen ? BV[t] : UY[t]; }
+  double* bdx() { return gen ? BDx : Dx; }
+  double* bdy() { return gen ? BDy : Dy; }
 
   lrep_status sync() {
     LCK(cudaStreamSynchronize(st));
@@ -220,6 +243,12 @@ struct Solver {
       UX[b] = blk(C); UY[b] = blk(C); KX[b] = blk(C); MY[b] = blk(C);
     }
     Dx = blk(r + nev); Dy = blk(r + nev); Q0 = blk(rr);
+    if (gen) {
+      for (int b = 0; b < 2; ++b) { BU[b] = blk(C); BV[b] = blk(C); }
+      BDx = blk(r + nev); BDy = blk(r + nev);
+      BWr = blk(cgcols); BZr = blk(cgcols); BT = blk(cgcols); BTW = blk(cgcols);
+      BTZ = blk(cgcols);
+    }
     Rhs = blk(cgcols); Zr = blk(cgcols); Wr = blk(cgcols); Rr = blk(cgcols);
     Pr = blk(cgcols); Qr = blk(cgcols); TW = blk(cgcols); TZ = blk(cgcols);
     Kh = A.take<double>(sm); Mh = A.take<double>(sm); Sh = A.take<double>(sm);
@@ -251,9 +280,9 @@ struct Solver {
     cg.counter = counters + 2;
   }
 
-  lrep_status alloc() {
-    const size_t key[4] = {(size_t)n, (size_t)nev, (size_t)nb,
-                           (size_t)(w * 1000 + r * 7 + p->opts.precision)};
+  // sizes of every workspace piece (alloc and bosp_footprint)
+  void plan() {
+    gen = p->op.hasB;
     ld = ((n + 31) / 32) * 32;
     cgcols = std::max(nb, std::max(r, 1));
     const int dd = 2 * dmax;
@@ -278,11 +307,22 @@ struct Solver {
     }
     part_elems = std::max(residual_ws_elems(n, std::max(C, nev)),
                           std::max(colnorm_ws_elems(n, cgcols), cg_part_elems(n, cgcols)));
+  }
+
+  size_t bytes_needed() {
+    plan();
     Arena dry;
     dry.base = nullptr;
     dry.cap = ~(size_t)0;
     layout(dry);
-    const size_t bytes = dry.off + 4096;
+    return dry.off + 4096;
+  }
+
+  lrep_status alloc() {
+    const size_t key[4] = {(size_t)n, (size_t)nev, (size_t)nb,
+                           (size_t)(w * 1000 + r * 7 + p->opts.precision +
+                                    (p->op.hasB ? 100000000 : 0))};
+    const size_t bytes = bytes_needed();
     Arena& A = p->ws;
     bool reuse = (A.base != nullptr) && A.cap >= bytes;
     for (int i = 0; i < 4; ++i) reuse = reuse && p->ws_key[i] == key[i];
@@ -419,13 +459,19 @@ struct Solver {
                            const double* KA, const double* MB, double* tA,
                            double* tB, double* tKA, double* tMB, double* outA,
                            double* outB, double* outKA, double* outMB,
-                           const double* refa2, const double* refb2, int* kept) {
+                           const double* refa2, const double* refb2, int* kept,
+                           const double* BAin = nullptr, const double* BBin = nullptr,
+                           double* tBA = nullptr, double* tBB = nullptr,
+                           double* outBA = nullptr, double* outBB = nullptr) {
     const double tau = p->opts.discard_tol;
     *kept = 0;
     if (m <= 0) return LREP_OK;
     const int ldg = 2 * dmax;
+    // Gram [A B]^T [BA BB]: the B-inner products when companions are given
+    const bool bc = BAin != nullptr;
     Segs s = seg_push(seg1(Ain, ld, m), Bin, ld, m);
-    LST(gram(s, s, G2, ldg));
+    Segs sb = bc ? seg_push(seg1(BAin, ld, m), BBin, ld, m) : s;
+    LST(gram(s, sb, G2, ldg));
     LCK(biorth_coef(m, G2, ldg, refa2, refb2, tau, cA, cB, dmax, cwork, cnt_d, st));
     LCK(cudaMemcpyAsync(&h->cnt[0], cnt_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     LST(sync());
@@ -437,8 +483,13 @@ struct Solver {
       LST(update(k1, 0.0, seg1(KA, ld, m), cA, dmax, 1.0, tKA));
       LST(update(k1, 0.0, seg1(MB, ld, m), cB, dmax, 1.0, tMB));
     }
+    if (bc) {
+      LST(update(k1, 0.0, seg1(BAin, ld, m), cA, dmax, 1.0, tBA));
+      LST(update(k1, 0.0, seg1(BBin, ld, m), cB, dmax, 1.0, tBB));
+    }
     Segs s2 = seg_push(seg1(tA, ld, k1), tB, ld, k1);
-    LST(gram(s2, s2, G2, ldg));
+    Segs s2b = bc ? seg_push(seg1(tBA, ld, k1), tBB, ld, k1) : s2;
+    LST(gram(s2, s2b, G2, ldg));
     LCK(biorth_coef(k1, G2, ldg, nullptr, nullptr, tau, cA2, cB2, dmax, cwork, cnt_d, st));
     LCK(cudaMemcpyAsync(&h->cnt[0], cnt_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     LST(sync());
@@ -449,6 +500,10 @@ struct Solver {
       LST(update(k2, 0.0, seg1(tKA, ld, k1), cA2, dmax, 1.0, outKA));
       LST(update(k2, 0.0, seg1(tMB, ld, k1), cB2, dmax, 1.0, outMB));
     }
+    if (bc) {
+      LST(update(k2, 0.0, seg1(tBA, ld, k1), cA2, dmax, 1.0, outBA));
+      LST(update(k2, 0.0, seg1(tBB, ld, k1), cB2, dmax, 1.0, outBB));
+    }
     *kept = k2;
     return LREP_OK;
   }
@@ -458,18 +513,24 @@ struct Solver {
     // generalized nullspace (eq. V0_basis)
     if (r > 0) {
       LCK(copy_cols(n, r, p->X0in, ld, Dx, ld, st));
+      // generalized LREP: M Y0 = B X0, X0^T B Y0 = I
+      if (gen) LST(apply(LREP_OP_B, r, Dx, BDx));
       if (p->Y0in) {
         LCK(copy_cols(n, r, p->Y0in, ld, Dy, ld, st));
       } else {
-        LST(cg_solve(LREP_OP_M, r, Dx, Dy, 1e-14, 20000, 50, false));
+        LST(cg_solve(LREP_OP_M, r, bdx(), Dy, 1e-14, 20000, 50, false));
       }
       double* T = UX[1];
-      LST(gram(seg1(Dx, ld, r), seg1(Dy, ld, r), Rg, r));
+      LST(gram(seg1(bdx(), ld, r), seg1(Dy, ld, r), Rg, r));
       LCK(chol_upper_inverse(r, Rg, r, Rinv, r, Rwork, info_d, st));
       LST(update(r, 0.0, seg1(Dx, ld, r), Rinv, r, 1.0, T));
       LCK(copy_cols(n, r, T, ld, Dx, ld, st));
       LST(update(r, 0.0, seg1(Dy, ld, r), Rinv, r, 1.0, T));
       LCK(copy_cols(n, r, T, ld, Dy, ld, st));
+      if (gen) {
+        LST(apply(LREP_OP_B, r, Dx, BDx));
+        LST(apply(LREP_OP_B, r, Dy, BDy));
+      }
       // orthonormal basis of span(X0) for the right-hand sides of K W = ...
       LCK(copy_cols(n, r, Dx, ld, Q0, ld, st));
       for (int pass = 0; pass < 2; ++pass) {
@@ -495,15 +556,23 @@ struct Solver {
     // Step 2: project off V0 (twice) and biorthogonalise
     if (r > 0) {
       for (int pass = 0; pass < 2; ++pass) {
-        LST(gram(seg1(Dy, ld, r), seg1(UX[0], ld, d0), Cproj, r));
+        LST(gram(seg1(bdy(), ld, r), seg1(UX[0], ld, d0), Cproj, r));
         LST(update(d0, 1.0, seg1(Dx, ld, r), Cproj, r, -1.0, UX[0]));
-        LST(gram(seg1(Dx, ld, r), seg1(UY[0], ld, d0), Cproj, r));
+        LST(gram(seg1(bdx(), ld, r), seg1(UY[0], ld, d0), Cproj, r));
         LST(update(d0, 1.0, seg1(Dy, ld, r), Cproj, r, -1.0, UY[0]));
       }
     }
     int kept = 0;
-    LST(biorth_block(UX[0], UY[0], d0, nullptr, nullptr, UX[1], UY[1], nullptr,
-                     nullptr, UX[0], UY[0], nullptr, nullptr, nullptr, nullptr, &kept));
+    if (gen) {
+      LST(apply(LREP_OP_B, d0, UX[0], BU[0]));
+      LST(apply(LREP_OP_B, d0, UY[0], BV[0]));
+      LST(biorth_block(UX[0], UY[0], d0, nullptr, nullptr, UX[1], UY[1], nullptr, nullptr,
+                       UX[0], UY[0], nullptr, nullptr, nullptr, nullptr, &kept, BU[0], BV[0],
+                       BU[1], BV[1], BU[0], BV[0]));
+    } else {
+      LST(biorth_block(UX[0], UY[0], d0, nullptr, nullptr, UX[1], UY[1], nullptr,
+                       nullptr, UX[0], UY[0], nullptr, nullptr, nullptr, nullptr, &kept));
+    }
     if (kept == 0) return p->fail(LREP_ERR_BREAKDOWN, "start block lost every column");
     cur = 0; off = 0; d = kept;
     LST(refresh());
@@ -514,6 +583,10 @@ struct Solver {
   lrep_status refresh() {
     LST(apply(LREP_OP_K, d, Ucur(), KUcur()));
     LST(apply(LREP_OP_M, d, Vcur(), MVcur()));
+    if (gen) {
+      LST(apply(LREP_OP_B, d, Ucur(), BUcur()));
+      LST(apply(LREP_OP_B, d, Vcur(), BVcur()));
+    }
     stale = false;
     return LREP_OK;
   }
@@ -527,7 +600,7 @@ struct Solver {
     if (events) LCK(cudaEventRecord(ev[0], st));
     LST(gram(sU, sKU, Kh, dmax));
     LST(gram(sV, sMV, Mh, dmax));
-    LST(gram(sU, sV, Sh, dmax));
+    LST(gram(sU, seg1(BVcur(), ld, d), Sh, dmax));  // U^T B V (safeguard)
     SmallJob job{};
     job.Khat = Kh; job.Mhat = Mh; job.ld_in = dmax; job.S = Sh;
     job.lam = lam_d; job.Xh = Xh; job.Yh = Yh; job.ldo = dmax;
@@ -542,9 +615,13 @@ struct Solver {
     LST(update(e, 0.0, sV, Yh, dmax, 1.0, UY[t]));
     LST(update(e, 0.0, sKU, Xh, dmax, 1.0, KX[t]));
     LST(update(e, 0.0, sMV, Yh, dmax, 1.0, MY[t]));
+    if (gen) {
+      LST(update(e, 0.0, seg1(BUcur(), ld, d), Xh, dmax, 1.0, BU[t]));
+      LST(update(e, 0.0, seg1(BVcur(), ld, d), Yh, dmax, 1.0, BV[t]));
+    }
     if (events) LCK(cudaEventRecord(ev[1], st));
     LCK(residuals_f64(n, e, UX[t], UY[t], KX[t], MY[t], ld, lam_d, eps_d, part,
-                      counters, st));
+                      counters, st, gen ? BU[t] : nullptr, gen ? BV[t] : nullptr));
     LCK(cudaMemcpyAsync(h->lam, lam_d, sizeof(double) * d, cudaMemcpyDeviceToHost, st));
     LCK(cudaMemcpyAsync(h->eps, eps_d, sizeof(double) * e, cudaMemcpyDeviceToHost, st));
     LCK(cudaMemcpyAsync(&h->berr, berr_d, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -588,8 +665,13 @@ struct Solver {
   lrep_status rebiorth() {
     const int t = nx();
     int kept = 0;
-    LST(biorth_block(Ucur(), Vcur(), d, KUcur(), MVcur(), UX[t], UY[t], KX[t], MY[t],
-                     UX[cur], UY[cur], KX[cur], MY[cur], nullptr, nullptr, &kept));
+    if (gen)
+      LST(biorth_block(Ucur(), Vcur(), d, KUcur(), MVcur(), UX[t], UY[t], KX[t], MY[t],
+                       UX[cur], UY[cur], KX[cur], MY[cur], nullptr, nullptr, &kept, BUcur(),
+                       BVcur(), BU[t], BV[t], BU[cur], BV[cur]));
+    else
+      LST(biorth_block(Ucur(), Vcur(), d, KUcur(), MVcur(), UX[t], UY[t], KX[t], MY[t],
+                       UX[cur], UY[cur], KX[cur], MY[cur], nullptr, nullptr, &kept));
     if (kept == 0) return p->fail(LREP_ERR_BREAKDOWN, "re-biorthogonalisation lost every column");
     off = 0;
     d = kept;
@@ -601,6 +683,12 @@ struct Solver {
     const int t = nx();
     LCK(copy_cols(n, count, UX[t] + (int64_t)first * ld, ld, Dx + (int64_t)(r + ell) * ld, ld, st));
     LCK(copy_cols(n, count, UY[t] + (int64_t)first * ld, ld, Dy + (int64_t)(r + ell) * ld, ld, st));
+    if (gen) {
+      LCK(copy_cols(n, count, BU[t] + (int64_t)first * ld, ld, BDx + (int64_t)(r + ell) * ld, ld,
+                    st));
+      LCK(copy_cols(n, count, BV[t] + (int64_t)first * ld, ld, BDy + (int64_t)(r + ell) * ld, ld,
+                    st));
+    }
     for (int i = 0; i < count; ++i) locked.push_back(h->lam[first + i]);
     ell += count;
     return LREP_OK;
@@ -622,8 +710,12 @@ struct Solver {
       int e = std::min(d, want_max + (moving ? 2 * nb : 0));
       LST(rayleigh_ritz_safe(&e));
       if (h->berr > p->opts.rebiorth_tol) {
+        // the safeguard fires on a basis that is biorthogonal to ~1e-12, so
+        // Alg. 1's coefficients are near the identity and K U, M V (B U,
+        // B V) follow them accurately: no fresh products here (the refresh
+        // schedule and the pre-decision refresh still apply)
         LST(rebiorth());
-        LST(refresh());
+        stale = true;
         e = std::min(d, std::min(w, d) + (moving ? 2 * nb : 0));
         LST(rayleigh_ritz_safe(&e));
       }
@@ -713,21 +805,36 @@ struct Solver {
     double* Wsol = Wr;
     double* Zsol = Zr;
     for (int sweep = 0; sweep < std::max(1, p->opts.ngs); ++sweep) {
-      // M Z = W Lambda + (X~ Lambda - M Y~)
-      LCK(gather_combine(n, na, act_d, lam_act, TX, -1.0, TM, sweep ? lam_act : nullptr,
-                         sweep ? Wsol : nullptr, ld, Rhs, ld, st));
+      // M Z = W Lambda + (X~ Lambda - M Y~); generalized: B W, B X~
+      if (gen && sweep) LST(apply(LREP_OP_B, na, Wsol, BT));
+      LCK(gather_combine(n, na, act_d, lam_act, bux(t), -1.0, TM, sweep ? lam_act : nullptr,
+                         sweep ? (gen ? BT : Wsol) : nullptr, ld, Rhs, ld, st));
       LST(cg_solve(LREP_OP_M, na, Rhs, Zsol, p->opts.cg_tol, p->opts.cg_maxit, 0, cgop));
-      // K W = Z Lambda + (Y~ Lambda - K X~), projected onto range(K)
-      LCK(gather_combine(n, na, act_d, lam_act, TY, -1.0, TK, lam_act, Zsol, ld, Rhs, ld, st));
+      // K W = Z Lambda + (Y~ Lambda - K X~), projected onto range(K);
+      // generalized: B Z, B Y~
+      if (gen) LST(apply(LREP_OP_B, na, Zsol, BT));
+      LCK(gather_combine(n, na, act_d, lam_act, bvy(t), -1.0, TK, lam_act, gen ? BT : Zsol, ld,
+                         Rhs, ld, st));
       if (r > 0) {
         LST(gram(seg1(Q0, ld, r), seg1(Rhs, ld, na), Cproj, r));
         LST(update(na, 1.0, seg1(Q0, ld, r), Cproj, r, -1.0, Rhs));
       }
       LST(cg_solve(LREP_OP_K, na, Rhs, Wsol, p->opts.cg_tol, p->opts.cg_maxit, 0, cgop));
     }
-    // entering norms for the discard rule
-    LCK(colnorm2_f64(n, na, Wsol, ld, refw2, part, counters + 1, st));
-    LCK(colnorm2_f64(n, na, Zsol, ld, refz2, part, counters + 1, st));
+    // entering norms for the discard rule (B-norms when generalized: B W, B Z
+    // are formed here and follow W, Z through the projections below)
+    if (gen) {
+      LST(apply(LREP_OP_B, na, Wsol, BWr));
+      LST(apply(LREP_OP_B, na, Zsol, BZr));
+      LST(gram(seg1(Wsol, ld, na), seg1(BWr, ld, na), G2, na));
+      diag_copy_kernel<<<1, 64, 0, st>>>(na, G2, na, refw2); LREP_COUNT_LAUNCH();
+      LST(gram(seg1(Zsol, ld, na), seg1(BZr, ld, na), G2, na));
+      diag_copy_kernel<<<1, 64, 0, st>>>(na, G2, na, refz2); LREP_COUNT_LAUNCH();
+      LCK(cudaGetLastError());
+    } else {
+      LCK(colnorm2_f64(n, na, Wsol, ld, refw2, part, counters + 1, st));
+      LCK(colnorm2_f64(n, na, Zsol, ld, refz2, part, counters + 1, st));
+    }
     // P~ = U P^, Q~ = V Q^ and their products by the same combinations
     LCK(cudaEventSynchronize(evp));
     const int pc = h->cnt[1];
@@ -738,24 +845,39 @@ struct Solver {
       LST(update(pc, 0.0, sV, Qh, dmax, 1.0, TY + (int64_t)end * ld));
       LST(update(pc, 0.0, sKU, Ph, dmax, 1.0, TK + (int64_t)end * ld));
       LST(update(pc, 0.0, sMV, Qh, dmax, 1.0, TM + (int64_t)end * ld));
+      if (gen) {
+        LST(update(pc, 0.0, seg1(BUcur(), ld, d), Ph, dmax, 1.0, BU[t] + (int64_t)end * ld));
+        LST(update(pc, 0.0, seg1(BVcur(), ld, d), Qh, dmax, 1.0, BV[t] + (int64_t)end * ld));
+      }
     }
     // eq. update_W / update_Z against [X0, X_locked, X~, P~] (applied twice)
     const int nw = wv + pc;
     const Segs SA = seg_push(seg1(Dx, ld, r + ell), TX + (int64_t)win0 * ld, ld, nw);
     const Segs SB = seg_push(seg1(Dy, ld, r + ell), TY + (int64_t)win0 * ld, ld, nw);
+    // B-companions: [B Dx, B X~, B P~], [B Dy, B Y~, B Q~]
+    const Segs SAb = seg_push(seg1(bdx(), ld, r + ell), bux(t) + (int64_t)win0 * ld, ld, nw);
+    const Segs SBb = seg_push(seg1(bdy(), ld, r + ell), bvy(t) + (int64_t)win0 * ld, ld, nw);
     const int L = r + ell + nw;
     for (int pass = 0; pass < 2; ++pass) {
-      LST(gram(SB, seg1(Wsol, ld, na), Cproj, L));
+      LST(gram(SBb, seg1(Wsol, ld, na), Cproj, L));
       LST(update(na, 1.0, SA, Cproj, L, -1.0, Wsol));
-      LST(gram(SA, seg1(Zsol, ld, na), Cproj, L));
+      if (gen) LST(update(na, 1.0, SAb, Cproj, L, -1.0, BWr));
+      LST(gram(SAb, seg1(Zsol, ld, na), Cproj, L));
       LST(update(na, 1.0, SB, Cproj, L, -1.0, Zsol));
+      if (gen) LST(update(na, 1.0, SBb, Cproj, L, -1.0, BZr));
     }
     // Alg. 1 on (W~, Z~) with the discard rule, into place after P~
     const int wpos = end + pc;
     int m = 0;
-    LST(biorth_block(Wsol, Zsol, na, nullptr, nullptr, TW, TZ, nullptr, nullptr,
-                     TX + (int64_t)wpos * ld, TY + (int64_t)wpos * ld, nullptr, nullptr,
-                     refw2, refz2, &m));
+    if (gen)
+      LST(biorth_block(Wsol, Zsol, na, nullptr, nullptr, TW, TZ, nullptr, nullptr,
+                       TX + (int64_t)wpos * ld, TY + (int64_t)wpos * ld, nullptr, nullptr,
+                       refw2, refz2, &m, BWr, BZr, BTW, BTZ, BU[t] + (int64_t)wpos * ld,
+                       BV[t] + (int64_t)wpos * ld));
+    else
+      LST(biorth_block(Wsol, Zsol, na, nullptr, nullptr, TW, TZ, nullptr, nullptr,
+                       TX + (int64_t)wpos * ld, TY + (int64_t)wpos * ld, nullptr, nullptr,
+                       refw2, refz2, &m));
     // fresh products K W~, M Z~
     LST(apply(LREP_OP_K, m, TX + (int64_t)wpos * ld, TK + (int64_t)wpos * ld));
     LST(apply(LREP_OP_M, m, TY + (int64_t)wpos * ld, TM + (int64_t)wpos * ld));
@@ -789,6 +911,18 @@ struct Solver {
     p->resid.assign(nc, 0.0);
     p->biorth_err = 0.0;
     if (nc == 0) return LREP_OK;
+    // biorthogonality of the result (X^T B Y; before the sign fix, which
+    // flips X, Y but not their B-companions)
+    if (nc <= 512) {
+      double* G = (2 * dmax * 2 * dmax >= nc * nc) ? G2 : nullptr;
+      if (G) {
+        LST(gram(seg1(p->Xres, ld, nc), seg1(bdy() + (int64_t)r * ld, ld, nc), G, nc));
+        LCK(biorth_error(nc, G, nc, berr_d, st));
+        LCK(cudaMemcpyAsync(&h->berr, berr_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+        LST(sync());
+        p->biorth_err = h->berr;
+      }
+    }
     LCK(fix_sign(n, nc, p->Xres, p->Yres, ld, st));
     LCK(cudaMemcpyAsync(lam_lock, locked.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st));
     // final residuals with fresh float64 products (eq. tol)
@@ -798,22 +932,15 @@ struct Solver {
       double* Y = p->Yres + (int64_t)c0 * ld;
       LST(apply(LREP_OP_K, cc, X, KX[0]));
       LST(apply(LREP_OP_M, cc, Y, MY[0]));
+      if (gen) {  // fresh B X, B Y into the free U, V buffers
+        LST(apply(LREP_OP_B, cc, X, UX[0]));
+        LST(apply(LREP_OP_B, cc, Y, UY[0]));
+      }
       LCK(residuals_f64(n, cc, X, Y, KX[0], MY[0], ld, lam_lock + c0, eps_d, part,
-                        counters, st));
+                        counters, st, gen ? UX[0] : nullptr, gen ? UY[0] : nullptr));
       LCK(cudaMemcpyAsync(h->eps, eps_d, sizeof(double) * cc, cudaMemcpyDeviceToHost, st));
       LST(sync());
       for (int i = 0; i < cc; ++i) p->resid[c0 + i] = h->eps[i];
-    }
-    // biorthogonality of the result
-    if (nc <= 512) {
-      double* G = (2 * dmax * 2 * dmax >= nc * nc) ? G2 : nullptr;
-      if (G) {
-        LST(gram(seg1(p->Xres, ld, nc), seg1(p->Yres, ld, nc), G, nc));
-        LCK(biorth_error(nc, G, nc, berr_d, st));
-        LCK(cudaMemcpyAsync(&h->berr, berr_d, sizeof(double), cudaMemcpyDeviceToHost, st));
-        LST(sync());
-        p->biorth_err = h->berr;
-      }
     }
     return LREP_OK;
   }
@@ -839,24 +966,7 @@ static void configure(Solver& S, lrep_problem p, int nev, int nb, double tol) {
 size_t bosp_footprint(lrep_problem p, int nev, int nb) {
   Solver S{};
   configure(S, p, nev, nb, 1.0);
-  S.ld = ((S.n + 31) / 32) * 32;
-  S.cgcols = std::max(S.nb, std::max(S.r, 1));
-  const int dd = 2 * S.dmax, rr = std::max(S.r, 1);
-  size_t wsz = 0;
-  wsz = std::max(wsz, gram_ws_elems(S.n, S.dmax, S.dmax));
-  wsz = std::max(wsz, gram_ws_elems(S.n, dd, dd));
-  wsz = std::max(wsz, gram_ws_elems(S.n, S.Lmax, S.cgcols));
-  wsz = std::max(wsz, gram_ws_elems(S.n, rr, std::max(rr, S.dmax)));
-  wsz = std::max(wsz, gram_ws_elems(S.n, nev, nev));
-  wsz = std::max(wsz, apply_ws_elems(p, std::max(S.C, S.cgcols)));
-  S.ws_elems = wsz;
-  S.part_elems = std::max(residual_ws_elems(S.n, std::max(S.C, nev)),
-                          std::max(colnorm_ws_elems(S.n, S.cgcols), cg_part_elems(S.n, S.cgcols)));
-  Arena dry;
-  dry.base = nullptr;
-  dry.cap = ~(size_t)0;
-  S.layout(dry);
-  return dry.off + 4096;
+  return S.bytes_needed();
 }
 
 lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol, SmallBatcher* batcher) {

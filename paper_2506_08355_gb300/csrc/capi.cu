@@ -273,6 +273,77 @@ lrep_status lrep_create_operator(lrep_problem* out, int64_t n, lrep_apply_fn fn,
   return LREP_OK;
 }
 
+lrep_status lrep_set_mass_dense(lrep_problem p, const double* B, int64_t ld, int32_t mem) {
+  if (!p) return LREP_ERR_ARG;
+  if (p->op.kind != OP_DENSE || !valid_mem(mem) || (B && ld < p->op.n))
+    return p->fail(LREP_ERR_ARG, "lrep_set_mass_dense: dense problem and ld >= n required");
+  const int64_t n = p->op.n;
+  if (!B) {
+    p->op.hasB = false;
+    p->op.B = nullptr;
+  } else if (mem == LREP_MEM_DEVICE_BORROW) {
+    if (ld != p->op.ld)
+      return p->fail(LREP_ERR_ARG, "lrep_set_mass_dense: a borrowed B needs the K, M leading "
+                                   "dimension");
+    p->op.B = const_cast<double*>(B);
+    p->op.hasB = true;
+  } else {
+    double* dst = nullptr;
+    PCK(p, cudaMalloc(&dst, sizeof(double) * p->op.ld * n));
+    p->op.owned.push_back(dst);
+    PCK(p, cudaMemcpy2DAsync(dst, p->op.ld * sizeof(double), B, ld * sizeof(double),
+                             n * sizeof(double), n, cudaMemcpyDefault, p->stream));
+    p->op.B = dst;
+    p->op.hasB = true;
+  }
+  PCK(p, cudaStreamSynchronize(p->stream));
+  // tensor-core forms of the operator now include (or drop) B
+  if (p->opts.precision != LREP_PREC_FP64) return build_split(p);
+  return LREP_OK;
+}
+
+lrep_status lrep_set_mass_csr(lrep_problem p, const int64_t* rowptr, const int32_t* colind,
+                              const double* values, int32_t mem) {
+  if (!p) return LREP_ERR_ARG;
+  if (p->op.kind != OP_CSR || !valid_mem(mem) || (rowptr && (!colind || !values)))
+    return p->fail(LREP_ERR_ARG, "lrep_set_mass_csr: CSR problem and all three arrays required");
+  const int64_t n = p->op.n;
+  if (!rowptr) {
+    p->op.hasB = false;
+    p->op.rpB = nullptr; p->op.ciB = nullptr; p->op.vB = nullptr;
+    return LREP_OK;
+  }
+  if (mem == LREP_MEM_DEVICE_BORROW) {
+    p->op.rpB = const_cast<int64_t*>(rowptr);
+    p->op.ciB = const_cast<int32_t*>(colind);
+    p->op.vB = const_cast<double*>(values);
+  } else {
+    int64_t nnz = 0;
+    if (mem == LREP_MEM_HOST) {
+      nnz = rowptr[n];
+    } else {
+      PCK(p, cudaMemcpyAsync(&nnz, rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             p->stream));
+      PCK(p, cudaStreamSynchronize(p->stream));
+    }
+    lrep_status s = copy_array(p, rowptr, n + 1, &p->op.rpB);
+    if (s == LREP_OK) s = copy_array(p, colind, nnz, &p->op.ciB);
+    if (s == LREP_OK) s = copy_array(p, values, nnz, &p->op.vB);
+    if (s != LREP_OK) return s;
+  }
+  p->op.hasB = true;
+  PCK(p, cudaStreamSynchronize(p->stream));
+  return LREP_OK;
+}
+
+lrep_status lrep_set_mass_callback(lrep_problem p, int32_t enable) {
+  if (!p) return LREP_ERR_ARG;
+  if (p->op.kind != OP_CALLBACK)
+    return p->fail(LREP_ERR_ARG, "lrep_set_mass_callback: callback problem required");
+  p->op.hasB = enable != 0;
+  return LREP_OK;
+}
+
 lrep_status lrep_set_nullspace(lrep_problem p, int32_t r, const double* X0,
                                const double* Y0, int64_t ld, int32_t mem) {
   if (!p) return LREP_ERR_ARG;
@@ -441,7 +512,7 @@ lrep_status lrep_destroy(lrep_problem p) {
 lrep_status lrep_op_apply(lrep_problem p, int32_t op, int32_t ncols, const double* X,
                           int64_t ldx, double* Y, int64_t ldy) {
   if (!p || !X || !Y || ncols < 0 || ldx < p->op.n || ldy < p->op.n ||
-      (op != LREP_OP_K && op != LREP_OP_M))
+      (op != LREP_OP_K && op != LREP_OP_M && !(op == LREP_OP_B && p->op.hasB)))
     return p ? p->fail(LREP_ERR_ARG, "lrep_op_apply: invalid argument") : LREP_ERR_ARG;
   const size_t ws = apply_ws_elems(p, ncols);
   if (p->op_arena.cap < (ws + 64) * sizeof(double))

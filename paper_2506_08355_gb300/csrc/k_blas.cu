@@ -339,7 +339,8 @@ namespace {
 __global__ void __launch_bounds__(256)
 residual_kernel(int64_t n, int w, const double* __restrict__ X,
                 const double* __restrict__ Y, const double* __restrict__ KX,
-                const double* __restrict__ MY, int64_t ld,
+                const double* __restrict__ MY, const double* __restrict__ BX,
+                const double* __restrict__ BY, int64_t ld,
                 const double* __restrict__ lam, double* __restrict__ eps,
                 double* __restrict__ part, unsigned int* counter,
                 int64_t slab_rows) {
@@ -351,7 +352,8 @@ residual_kernel(int64_t n, int w, const double* __restrict__ X,
   double s1 = 0, s2 = 0, s3 = 0, s4 = 0;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     const double x = X[off + i], y = Y[off + i];
-    const double a = KX[off + i] - l * y, b = MY[off + i] - l * x;
+    const double bx = BX ? BX[off + i] : x, by = BY ? BY[off + i] : y;
+    const double a = KX[off + i] - l * by, b = MY[off + i] - l * bx;
     s1 = fma(a, a, s1); s2 = fma(b, b, s2); s3 = fma(x, x, s3); s4 = fma(y, y, s4);
   }
   s1 = block_sum(s1, red); s2 = block_sum(s2, red);
@@ -379,12 +381,13 @@ size_t residual_ws_elems(int64_t n, int w) {
 cudaError_t residuals_f64(int64_t n, int w, const double* X, const double* Y,
                           const double* KX, const double* MY, int64_t ld,
                           const double* lam, double* eps, double* part,
-                          unsigned int* counter, cudaStream_t st) {
+                          unsigned int* counter, cudaStream_t st, const double* BX,
+                          const double* BY) {
   if (w <= 0) return cudaSuccess;
   const int slabs = reduction_slabs(n, 2048, 64);
   const int64_t slab_rows = (n + slabs - 1) / slabs;
   dim3 grid(slabs, w);
-  residual_kernel<<<grid, 256, 0, st>>>(n, w, X, Y, KX, MY, ld, lam, eps, part,
+  residual_kernel<<<grid, 256, 0, st>>>(n, w, X, Y, KX, MY, BX, BY, ld, lam, eps, part,
                                         counter, slab_rows); LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -79,18 +79,13 @@ __device__ bool chol_lower(double* L, int d, int* s_flag) {
 //  2. FP64 refinement of the right factor V by matrix products: two
 //     Newton-Schulz steps V <- V - V (V^T V - I)/2, then steps of
 //     simultaneous Jacobi rotations B = G V, C = B^T B, t_ab from the 2 x 2
-//     problem of columns (a, b), V <- V (I + T - T^T), each followed by two
+//     problem of columns (a, b), V <- V (I + T - T^T), each followed by three
 //     Newton-Schulz steps, until max cos < d eps (quadratic convergence).
 // The column products of B keep each pair's rounding relative to
 // sigma_a sigma_b, so small singular values keep relative accuracy.
 // dyn: dynamic shared memory (dyn_bytes); matrices are column-major with
 // leading dimension d.
 
-__device__ __forceinline__ float warp_sumf(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // C = A * B (+ beta C) for d x d column-major matrices (ld d); C must not
 // alias A or B.  transA: use A^T.
@@ -121,9 +116,9 @@ __device__ __forceinline__ double pair_rotation(double aa, double bb, double g) 
 // where |t| <= kRotCap; larger rotations (relative gap of the pair's singular
 // values below ~cos / kRotCap, e.g. a degenerate cluster) are done exactly,
 // one pair at a time, after the simultaneous steps.  A first-order step
-// leaves V non-orthogonal by O(t^2) <= 1e-6, which two Newton-Schulz steps
-// take below rounding (1e-6 -> ~1e-12 -> ~1e-24).
-constexpr double kRotCap = 1e-3;
+// leaves V non-orthogonal by O(t^2) <= 2.5e-3, which three Newton-Schulz
+// steps take below rounding (2.5e-3 -> ~1e-5 -> ~1.5e-10 -> ~3e-20).
+constexpr double kRotCap = 0.05;
 constexpr int kMaxPairs = 512;
 
 // Newton-Schulz step: V <- V - V (V^T V - I) / 2, using R and T as scratch.
@@ -171,7 +166,6 @@ __device__ SmallMats small_place(const SmallJob& J, double* dyn, int dyn_bytes) 
 __device__ bool small_phase1(const SmallJob& J, const SmallMats& mm, int* sweeps_out) {
   const int d = J.d;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   __shared__ int s_flag;
   __shared__ int s_conv;
   __shared__ double red[32];
@@ -218,29 +212,44 @@ __device__ bool small_phase1(const SmallJob& J, const SmallMats& mm, int* sweeps
   // ---- phase 1: FP32 one-sided Jacobi
   const int dp = d + (d & 1), m = dp - 1;
   const float tol32 = 2.0f * sqrtf((float)d) * 1.1920929e-7f;
+  const int npairs = dp / 2;
+  int gsz = 32;
+  while (gsz > 16 && npairs > nt / gsz) gsz >>= 1;
+  const int ngroups = nt / gsz, gid = tid / gsz, glane = tid % gsz;
   int sweeps = 0;
   for (int sweep = 0; sweep < 30; ++sweep) {
     ++sweeps;
     if (tid == 0) s_conv = 1;
     __syncthreads();
     for (int r = 0; r < m; ++r) {
-      for (int p = wid; p < dp / 2; p += nw) {
-        int a, b;
-        if (p == 0) { a = r; b = m; }
-        else { a = (r + p) % m; b = (r - p + m) % m; }
-        if (a > b) { const int t = a; a = b; b = t; }
-        if (b >= d) continue;
-        float al = 0.f, be = 0.f, ga = 0.f;
-        for (int i = lane; i < d; i += 32) {
-          const float x = G32[i + a * d], y = G32[i + b * d];
-          al = fmaf(x, x, al); be = fmaf(y, y, be); ga = fmaf(x, y, ga);
+      // the pairs of the round in lane groups of gsz lanes (16 or 32: one
+      // group per pair when they fit); every lane runs the same trip count
+      // (inactive groups idle through the shuffles)
+      for (int base = 0; base < npairs; base += ngroups) {
+        const int p = base + gid;
+        int a = 0, b = 0;
+        if (p < npairs) {
+          if (p == 0) { a = r; b = m; }
+          else { a = (r + p) % m; b = (r - p + m) % m; }
+          if (a > b) { const int t = a; a = b; b = t; }
         }
-        al = warp_sumf(al); be = warp_sumf(be); ga = warp_sumf(ga);
-        if (fabsf(ga) > tol32 * sqrtf(al * be)) {
+        const bool live = p < npairs && b < d;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        if (live)
+          for (int i = glane; i < d; i += gsz) {
+            const float x = G32[i + a * d], y = G32[i + b * d];
+            al = fmaf(x, x, al); be = fmaf(y, y, be); ga = fmaf(x, y, ga);
+          }
+        for (int o = gsz >> 1; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (live && fabsf(ga) > tol32 * sqrtf(al * be)) {
           const float zeta = (be - al) / (2.0f * ga);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
           const float c = rsqrtf(1.f + t * t), s = c * t;
-          for (int i = lane; i < d; i += 32) {
+          for (int i = glane; i < d; i += gsz) {
             const float x = G32[i + a * d], y = G32[i + b * d];
             G32[i + a * d] = c * x - s * y;
             G32[i + b * d] = s * x + c * y;
@@ -248,7 +257,7 @@ __device__ bool small_phase1(const SmallJob& J, const SmallMats& mm, int* sweeps
             V32[i + a * d] = c * u - s * v;
             V32[i + b * d] = s * u + c * v;
           }
-          if (lane == 0) s_conv = 0;
+          if (glane == 0) s_conv = 0;
         }
       }
       __syncthreads();
@@ -336,6 +345,7 @@ __device__ void small_lrep_body(const SmallJob& J, double* dyn, int dyn_bytes) {
     __syncthreads();
     mm_d(d, V, false, S, B, 1.0, 1.0);            // B = V + V Omega
     { double* t = V; V = B; B = t; }
+    ns_step(d, V, B, S);
     ns_step(d, V, B, S);
     ns_step(d, V, B, S);
   }
@@ -442,7 +452,7 @@ __global__ void __launch_bounds__(SMALL_T) small_lrep_one_kernel(SmallJob J, int
 // of V and the Ritz coefficients run as grid kernels (every d x d product
 // over ceil(d/16)^2 CTAs), so the FP64 work uses many SMs instead of one.
 // Same arithmetic as the one-CTA path: two Newton-Schulz steps, up to six
-// steps of simultaneous rotations (+ two Newton-Schulz steps each), exact
+// steps of simultaneous rotations (+ three Newton-Schulz steps each), exact
 // sequential rotations of the nearly degenerate pairs, then X^, Y^.
 // Work layout (doubles, after L1, L2): G, V, T, R, B, S (d^2 each), then the
 // control block.
@@ -761,6 +771,7 @@ cudaError_t small_lrep_wide(const SmallJob& J, cudaStream_t st) {
     sq_check_kernel<<<1, 1, 0, st>>>(w.ctl, it, tol, it == 5); LREP_COUNT_LAUNCH();
     gemm(w.V, 0, w.R, w.T, 1.0, w.V, 1.0, 0.0, stop);       // T = V + V Omega
     copy(w.T, w.V, stop);
+    ns(stop);
     ns(stop);
     ns(stop);
   }

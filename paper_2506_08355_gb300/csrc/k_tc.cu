@@ -5,9 +5,9 @@
 // split per call.  The three products accumulate in one fp32 tensor-memory
 // accumulator (tcgen05.mma kind::f16, M = 128 rows, N = columns rounded up
 // to 16).  Operand tiles (64 k-values = 128 bytes per row, 128-byte
-// swizzle) are staged by TMA through a 4-stage mbarrier pipeline; one
-// thread issues TMA, one issues MMA, and four warps drain the accumulator
-// with tcgen05.ld.  Split-K partials (fp32) are summed in a fixed order in
+// swizzle) are staged by TMA through a 3-stage mbarrier pipeline (two CTAs
+// per SM); one thread issues TMA, one issues MMA, and four warps drain the
+// accumulator with tcgen05.ld.  Split-K partials (fp32) are summed in a fixed order in
 // fp64.  Relative error ~ 2^-16 plus fp32 accumulation, far below the CG
 // tolerance (1e-2) that these products serve.
 //
@@ -30,12 +30,12 @@ namespace {
 
 constexpr int BM = 128;              // output rows per CTA = TMEM lanes
 constexpr int BK = 64;               // k per stage: 64 bf16 = 128 B (one swizzle row)
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;             // 3 x ~36 KB: two CTAs per SM
 constexpr int TILE_A = BM * BK * 2;  // 16 KB
 
 using namespace tc5;
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
 bf16x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
               const __grid_constant__ CUtensorMap mXhi, const __grid_constant__ CUtensorMap mXlo,
               int n, int c, int N, int kt_per_split, int kt_total, int tmem_cols,
@@ -211,11 +211,28 @@ EncodeTiledFn encoder() {
   return fn;
 }
 
-int tc_splits(int64_t n) {
+// k-tiles per split: fewest waves of 2 x 152 resident CTAs x (tiles per CTA
+// + pipeline fill)
+int tc_per(int64_t n) {
   const int64_t tiles = (n + BM - 1) / BM;
   const int64_t kt = (n + BK - 1) / BK;
-  int64_t s = (2 * kNumSMs + tiles - 1) / tiles;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(s, kt));
+  const int64_t slots = 2 * (int64_t)kNumSMs;
+  int64_t best = -1, best_cost = 0;
+  for (int64_t per = 1; per <= kt; ++per) {
+    const int64_t s = (kt + per - 1) / per;
+    const int64_t cost = ((tiles * s + slots - 1) / slots) * (per + 2);
+    if (best < 0 || cost <= best_cost) {
+      best = per;
+      best_cost = cost;
+    }
+  }
+  return (int)best;
+}
+
+int tc_splits(int64_t n) {
+  const int64_t kt = (n + BK - 1) / BK;
+  const int per = tc_per(n);
+  return (int)((kt + per - 1) / per);
 }
 
 }  // namespace
@@ -268,9 +285,8 @@ cudaError_t tc_apply(const TcOperand& A, int64_t n, int c, const double* X, int6
   if (!tc_make_map(&mxh, xhi, n, c, ldb, BK, N) || !tc_make_map(&mxl, xlo, n, c, ldb, BK, N))
     return cudaErrorInvalidValue;
   const int kt = (int)((n + BK - 1) / BK);
-  int s = tc_splits(n);
-  const int per = (kt + s - 1) / s;
-  s = (kt + per - 1) / per;
+  const int per = tc_per(n);
+  const int s = (kt + per - 1) / per;
   int tcols = 32;
   while (tcols < N) tcols <<= 1;
   const int tile_x = N * BK * 2;

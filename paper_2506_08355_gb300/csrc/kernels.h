@@ -47,10 +47,13 @@ cudaError_t update_f64(int64_t n, int c, double alpha, const Segs& A,
 // eq. tol residuals for w columns; part >= residual_ws_elems(n, w);
 // counter: one zero-initialised word owned by the caller.
 size_t residual_ws_elems(int64_t n, int w);
+// BX, BY (optional): B X, B Y of the generalized LREP for the lam terms
+// (K X - lam B Y, M Y - lam B X); the denominator keeps ||[Y; X]||.
 cudaError_t residuals_f64(int64_t n, int w, const double* X, const double* Y,
                           const double* KX, const double* MY, int64_t ld,
                           const double* lam, double* eps, double* part,
-                          unsigned int* counter, cudaStream_t st);
+                          unsigned int* counter, cudaStream_t st,
+                          const double* BX = nullptr, const double* BY = nullptr);
 
 // out[:, b] = s1[b] * P1[:, idx[b]] + s2 * P2[:, idx[b]] + (P3 ? s3[b] * P3[:, b] : 0)
 cudaError_t gather_combine(int64_t n, int nb, const int* idx, const double* s1,

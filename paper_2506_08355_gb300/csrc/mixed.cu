@@ -25,15 +25,15 @@ bool split_ready(lrep_problem p) {
   const Operator& o = p->op;
   const bool dense = o.kind == OP_DENSE;
   return (p->opts.precision == LREP_PREC_FP64 || o.tc_err) && (!want_tc(p) || o.tcK) &&
-         (!want_oz(p) || !dense || o.ozK);
+         (!want_oz(p) || !dense || (o.ozK && (!o.hasB || o.ozB)));
 }
 
 size_t split_bytes(lrep_problem p) {
   const int64_t n = p->op.n;
   size_t b = 0;
   if (want_tc(p)) b += (size_t)2 * 2 * 2 * tc_ld(n) * n;  // K, M x (hi, lo) bf16
-  if (want_oz(p) && p->op.kind == OP_DENSE)
-    b += (size_t)2 * oz_operand_bytes(n);                 // K, M x 7 digit planes
+  if (want_oz(p) && p->op.kind == OP_DENSE)               // K, M (B) x 7 digit planes
+    b += (size_t)(p->op.hasB ? 3 : 2) * oz_operand_bytes(n);
   return b;
 }
 
@@ -72,15 +72,17 @@ lrep_status build_split(lrep_problem p) {
     }
   }
   if (want_oz(p) && o.kind == OP_DENSE) {
-    OzOperand* z[2] = {new OzOperand(), new OzOperand()};
+    OzOperand* z[3] = {new OzOperand(), new OzOperand(), o.hasB ? new OzOperand() : nullptr};
     o.ozK = z[0];
     o.ozM = z[1];
-    for (int i = 0; i < 2; ++i) {
+    o.ozB = z[2];
+    const double* src3[3] = {o.K, o.M, o.B};
+    for (int i = 0; i < (o.hasB ? 3 : 2); ++i) {
       if (cudaMalloc(&z[i]->slices, oz_operand_bytes(n)) != cudaSuccess) {
         free_split(p);
         return p->fail(LREP_ERR_NOMEM, "digit planes of the operator: out of device memory");
       }
-      const cudaError_t e = oz_slice_operator(n, src[i], o.ld, z[i], p->stream);
+      const cudaError_t e = oz_slice_operator(n, src3[i], o.ld, z[i], p->stream);
       if (e != cudaSuccess) {
         free_split(p);
         return p->fail(LREP_ERR_CUDA, std::string("digit planes: ") + cudaGetErrorString(e));
@@ -106,7 +108,7 @@ void free_split(lrep_problem p) {
       *t = nullptr;
     }
   }
-  for (OzOperand** z : {&o.ozK, &o.ozM}) {
+  for (OzOperand** z : {&o.ozK, &o.ozM, &o.ozB}) {
     if (*z) {
       if ((*z)->slices) cudaFree((*z)->slices);
       delete *z;
@@ -127,7 +129,8 @@ size_t apply_cg_ws_elems(lrep_problem p, int c) {
 lrep_status apply_sliced(lrep_problem p, int which, int c, const double* X, int64_t ldx,
                          double* Y, int64_t ldy, const int* skip, double* ws, size_t ws_elems) {
   const Operator& o = p->op;
-  cudaError_t e = oz_apply(which == LREP_OP_K ? *o.ozK : *o.ozM, c, X, ldx, Y, ldy, ws,
+  const OzOperand& A = which == LREP_OP_K ? *o.ozK : which == LREP_OP_M ? *o.ozM : *o.ozB;
+  cudaError_t e = oz_apply(A, c, X, ldx, Y, ldy, ws,
                            ws_elems * sizeof(double), o.tc_err, skip, p->stream);
   if (e != cudaSuccess)
     return p->fail(LREP_ERR_CUDA, std::string("sliced product: ") + cudaGetErrorString(e));

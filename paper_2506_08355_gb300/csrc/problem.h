@@ -55,6 +55,13 @@ struct Operator {
   // callback
   lrep_apply_fn fn = nullptr;
   void* user = nullptr;
+  // mass matrix B of the generalized LREP (none: B = I)
+  bool hasB = false;
+  double* B = nullptr;  // dense (ld)
+  int64_t* rpB = nullptr;  // csr
+  int32_t* ciB = nullptr;
+  double* vB = nullptr;
+  struct OzOperand* ozB = nullptr;  // digit planes of dense B (FP64_SLICED)
   // mixed precision: bf16 hi/lo split of dense K and M (tc.h)
   struct TcOperand* tcK = nullptr;
   struct TcOperand* tcM = nullptr;

@@ -21,7 +21,7 @@ ERR = {-1: "ERR_ARG", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_NOT_SPD",
        -5: "ERR_BREAKDOWN", -6: "ERR_TIMEOUT", -7: "ERR_STATE", -8: "ERR_CALLBACK"}
 MEM_HOST, MEM_DEVICE_COPY, MEM_DEVICE_BORROW = 0, 1, 2
 FORM_AB, FORM_KM = 0, 1
-OP_K, OP_M = 0, 1
+OP_K, OP_M, OP_B = 0, 1, 2
 PREC_FP64, PREC_MIXED_BF16X3, PREC_FP64_SLICED, PREC_MIXED_SLICED = 0, 1, 2, 3
 (Q_NCONV, Q_EIGVALS, Q_X, Q_Y, Q_U, Q_V, Q_RESID, Q_ITERS, Q_MATVECS, Q_TIMINGS,
  Q_BIORTH_ERR, Q_HISTORY, Q_REBIORTHS, Q_PROFILE, Q_PROFILE_CG) = range(15)
@@ -57,6 +57,10 @@ EXPORTS = {
     "lrep_find_nullspace": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32,
                                       C.c_void_p, C.c_int64, C.c_int32,
                                       C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lrep_set_mass_dense": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32]),
+    "lrep_set_mass_csr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_int32]),
+    "lrep_set_mass_callback": (C.c_int, [C.c_void_p, C.c_int32]),
     "lrep_set_options": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
     "lrep_set_start": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.c_int64, C.c_int32]),
@@ -284,6 +288,34 @@ class Problem:
         _check(lib().lrep_find_nullspace(self.h, r_max, tol, maxit, _ptr(out), self.n, MEM_HOST,
                                          C.byref(r), C.byref(it)), self.h)
         return out[: r.value].T.copy(), it.value
+
+    def set_mass(self, Bm=None, borrow=False):
+        """Mass matrix B of the generalized LREP: a dense (n, n) array or
+        device tensor for dense problems, a CSR triple for CSR problems,
+        True for a callback problem (the callback is asked for op OP_B);
+        None clears it."""
+        L = lib()
+        if isinstance(Bm, bool):
+            _check(L.lrep_set_mass_callback(self.h, int(Bm)), self.h)
+        elif Bm is None:
+            st = L.lrep_set_mass_dense(self.h, None, self.n, MEM_HOST)
+            if st < 0:
+                st = L.lrep_set_mass_csr(self.h, None, None, None, MEM_HOST)
+            _check(st, self.h)
+        elif isinstance(Bm, tuple):
+            rp, ci, va = (np.ascontiguousarray(Bm[0], dtype=np.int64),
+                          np.ascontiguousarray(Bm[1], dtype=np.int32),
+                          np.ascontiguousarray(Bm[2], dtype=np.float64))
+            self._keep.extend([rp, ci, va])
+            _check(L.lrep_set_mass_csr(self.h, _ptr(rp), _ptr(ci), _ptr(va), MEM_HOST), self.h)
+        elif _is_torch(Bm):
+            mem = MEM_DEVICE_BORROW if borrow else MEM_DEVICE_COPY
+            if borrow:
+                self._keep.append(Bm)
+            _check(L.lrep_set_mass_dense(self.h, _ptr(Bm), Bm.stride(0), mem), self.h)
+        else:
+            b, ld = _host_block(Bm)
+            _check(L.lrep_set_mass_dense(self.h, _ptr(b), ld, MEM_HOST), self.h)
 
     def set_options(self, **kw):
         o = default_options(**kw)
