@@ -110,6 +110,42 @@ class StencilOp:
         return Y[:, 0] if vec else Y
 
 
+class SpectralOp:
+    """lap_coef * Lap_F + diag(d) on a periodic nx*ny*nz grid of a box with
+    side lengths L (the Fourier spectral discretisation of the BdG example,
+    Section 4, Example "large-scale dense matrix", eq. bdg_KM).
+
+    Lap_F x = ifftn(-|kappa|^2 fftn(x)) over the whole grid, kappa_d =
+    2 pi m / L_d for the signed frequencies m of numpy's fftfreq order (the
+    Nyquist mode m = -N_d/2 keeps its kappa^2); index i + nx*(j + ny*k).
+    Parity: pinned (closed-form Fourier second-derivative matrix, plane
+    waves, harmonic-oscillator spectrum, Table 8).
+    """
+
+    def __init__(self, nx, ny, nz, L, lap_coef, dK, dM):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.n = nx * ny * nz
+        kap = [2.0 * np.pi / float(Ld) * np.fft.fftfreq(Nd, 1.0 / Nd)
+               for Nd, Ld in zip((nx, ny, nz), L)]
+        k2 = (kap[2][:, None, None] ** 2 + kap[1][None, :, None] ** 2
+              + kap[0][None, None, :] ** 2)
+        self.mult = -float(lap_coef) * k2  # Fourier multiplier of lap_coef * Lap_F
+        self.dK = np.asarray(dK, dtype=np.float64)
+        self.dM = np.asarray(dM, dtype=np.float64)
+
+    def apply(self, which, X):
+        X = np.asarray(X, dtype=np.float64)
+        vec = X.ndim == 1
+        Xc = X.reshape(self.n, -1)
+        c = Xc.shape[1]
+        G = Xc.reshape(self.nz, self.ny, self.nx, c)
+        F = np.fft.fftn(G, axes=(0, 1, 2))
+        L = np.real(np.fft.ifftn(self.mult[..., None] * F, axes=(0, 1, 2)))
+        d = self.dK if which == "K" else self.dM
+        Y = L.reshape(self.n, c) + d[:, None] * Xc
+        return Y[:, 0] if vec else Y
+
+
 class CsrOp:
     """K, M given as CSR triples (rowptr, colind, values)."""
 

@@ -21,6 +21,12 @@ Workloads (shapes follow the paper's examples, Section 4):
   h^3 sum phi^2 = 1, and d_K is chosen pointwise as (1/2 Lap_h phi)/phi so
   that K phi = 0 exactly: phi is K's null vector, as the condensate is for
   L_GP in the paper.  d_M = d_K + 2 g phi^2 (the B = g phi^2 coupling).
+* ``bdg_spectral``: the BdG example itself in its Fourier spectral form on
+  the periodic box (-8, 8)^3 (beta = 100, gamma = (1, 1, 2)), around the
+  discrete Gross-Pitaevskii ground state from ``gpe_ground_state`` (a
+  nonlinear input solve with its own FFT Laplacian; it is not the
+  eigensolver's operator product, which the oracle and the CUDA path each
+  implement).
 """
 from __future__ import annotations
 
@@ -165,6 +171,142 @@ def bdg_stencil(nx: int, ny: int = None, nz: int = None, g: float = 1.0,
     return {"dK": dK, "dM": dM, "phi": unit, "h": h, "nx": nx, "ny": ny,
             "nz": nz, "n": nx * ny * nz, "v1d": vs, "coords": coords,
             "lap_coef": -0.5}
+
+
+# --------------------------------------------------------------------------
+# Fourier spectral BdG (Example "large-scale dense matrix", eq. bdg, bdg_KM)
+
+
+def _spectral_grid(dims, lengths):
+    """Periodic grid x_j = -L/2 + j h, h = L / N per axis (x = 0 on a flat
+    axis with N = 1; arrays in (z, y, x) order, x fastest) and the squared
+    wave numbers of rfftn."""
+    nx, ny, nz = dims
+    coords = [(-0.5 * Ld + np.arange(Nd) * (Ld / Nd)) if Nd > 1 else np.zeros(1)
+              for Nd, Ld in zip(dims, lengths)]
+    kap = [2.0 * math.pi / Ld * np.fft.fftfreq(Nd, 1.0 / Nd) for Nd, Ld in zip(dims, lengths)]
+    kx2 = (2.0 * math.pi / lengths[0] * np.fft.rfftfreq(nx, 1.0 / nx)) ** 2
+    k2 = (kap[2][:, None, None] ** 2 + kap[1][None, :, None] ** 2 + kx2[None, None, :])
+    return coords, k2
+
+
+def gpe_ground_state(dims, lengths=(16.0, 16.0, 16.0), beta=100.0, gamma=(1.0, 1.0, 2.0),
+                     flow_tol=1e-5, newton_tol=1e-13):
+    """Discrete ground state of the Gross-Pitaevskii equation (eq. gpe) in
+    the Fourier spectral discretisation on the periodic box: the positive
+    phi_s with h^3 sum phi_s^2 = 1 and
+    [-1/2 Lap_F + V + beta phi_s^2] phi_s = mu_s phi_s,
+    V = 1/2 sum_d (gamma_d x_d)^2.  It is an input of the BdG workload
+    (the condensate the excitations are computed around), not part of the
+    eigensolver.
+
+    Computed by a normalised gradient flow (backward-Euler Fourier step
+    with a constant stabilising shift) to flow_tol, then Newton steps on
+    (phi, mu) with the normalisation constraint; the Newton system is solved
+    with two preconditioned CG solves with L + 2 beta phi^2 (SPD near the
+    ground state).  Returns (phi_s, mu_s, V, residual max-norm)."""
+    dims = tuple(int(d) for d in dims)
+    nx, ny, nz = dims
+    coords, k2 = _spectral_grid(dims, lengths)
+    hvol = float(np.prod([Ld / Nd for Nd, Ld in zip(dims, lengths) if Nd > 1]))
+    shape = (nz, ny, nx)
+    z, y, x = coords[2][:, None, None], coords[1][None, :, None], coords[0][None, None, :]
+    V = 0.5 * ((gamma[0] * x) ** 2 + (gamma[1] * y) ** 2 + (gamma[2] * z) ** 2)
+    V = np.broadcast_to(V, shape).copy()
+
+    def half_lap(u):  # -1/2 Lap_F u
+        return np.fft.irfftn(0.5 * k2 * np.fft.rfftn(u), s=shape, axes=(0, 1, 2))
+
+    def normalise(u):
+        return u / math.sqrt(hvol * float(np.sum(u * u)))
+
+    phi = normalise(np.exp(-0.5 * (gamma[0] * x * x + gamma[1] * y * y + gamma[2] * z * z))
+                    * np.ones(shape))
+    tau = 0.5
+    for _ in range(20000):
+        w = V + beta * phi * phi
+        alpha = 0.5 * (float(w.max()) + float(w.min()))
+        rhs = (1.0 / tau + alpha - w) * phi
+        new = normalise(np.fft.irfftn(np.fft.rfftn(rhs) / (1.0 / tau + alpha + 0.5 * k2),
+                                      s=shape, axes=(0, 1, 2)))
+        step = float(np.abs(new - phi).max())
+        phi = new
+        if step < flow_tol:
+            break
+
+    def pcg(op, b, tol=1e-14, maxit=5000):
+        pre = lambda r: np.fft.irfftn(np.fft.rfftn(r) / (0.5 * k2 + 10.0), s=shape,
+                                      axes=(0, 1, 2))
+        xk = np.zeros_like(b)
+        r = b.copy()
+        zr = pre(r)
+        p = zr.copy()
+        rz = float(np.sum(r * zr))
+        nb = math.sqrt(float(np.sum(b * b)))
+        for _ in range(maxit):
+            q = op(p)
+            a = rz / float(np.sum(p * q))
+            xk += a * p
+            r -= a * q
+            if math.sqrt(float(np.sum(r * r))) <= tol * nb:
+                break
+            zr = pre(r)
+            rz2 = float(np.sum(r * zr))
+            p = zr + (rz2 / rz) * p
+            rz = rz2
+        return xk
+
+    res = np.inf
+    for _ in range(12):
+        Aphi = half_lap(phi) + (V + beta * phi * phi) * phi
+        mu = hvol * float(np.sum(phi * Aphi))
+        F1 = Aphi - mu * phi
+        res = float(np.abs(F1).max())
+        if res < newton_tol:
+            break
+        wM = V + 3.0 * beta * phi * phi - mu
+        opM = lambda u: half_lap(u) + wM * u
+        a = pcg(opM, F1)
+        b = pcg(opM, phi)
+        dmu = float(np.sum(phi * a)) / float(np.sum(phi * b))
+        phi = normalise(phi - a + dmu * b)
+    Aphi = half_lap(phi) + (V + beta * phi * phi) * phi
+    mu = hvol * float(np.sum(phi * Aphi))
+    res = float(np.abs(Aphi - mu * phi).max())
+    return phi.reshape(-1), mu, V.reshape(-1), res
+
+
+def bdg_spectral(nx: int, ny: int = None, nz: int = None, box=(16.0, 16.0, 16.0),
+                 beta: float = 100.0, gamma=(1.0, 1.0, 2.0)):
+    """The 3-D BdG workload of the paper's "large-scale dense matrix"
+    example in its Fourier spectral form: box (-8, 8)^3, beta = 100,
+    gamma = (1, 1, 2), n = nx*ny*nz (Table 8: nx = 16, 32, 64, 128, 256 for
+    h = h0 ... h0/16).  K = -1/2 Lap_F + dK and M = -1/2 Lap_F + dM with
+    dK = V + beta phi_s^2 - mu_s and dM = dK + 2 beta phi_s^2 (eq. bdg_KM:
+    K = L_GP, M = L_GP + 2 beta |phi_s|^2), so K phi_s = 0 up to the ground
+    state's residual.  Returns dK, dM, phi (unit 2-norm, the null vector of
+    K), phi_s (h^3-normalised), mu, V, lengths and the grid sizes."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    dims = (nx, ny, nz)
+
+    def make():
+        phi_s, mu, V, res = gpe_ground_state(dims, box, beta, gamma)
+        dK = V + beta * phi_s * phi_s - mu
+        return {"dK": dK, "dM": dK + 2.0 * beta * phi_s * phi_s, "phi_s": phi_s,
+                "mu": mu, "V": V, "gpe_residual": res}
+
+    n = nx * ny * nz
+    if n >= 32768:
+        key = "bdg_spectral_%dx%dx%d_b%g_g%g_%g_%g_L%g_%g_%g" % (dims + (beta,) + tuple(gamma)
+                                                              + tuple(box))
+        out = _cached(key, make)
+    else:
+        out = make()
+    phi = out["phi_s"] / np.linalg.norm(out["phi_s"])
+    out.update(phi=phi, lengths=np.asarray(box, dtype=np.float64), nx=nx, ny=ny, nz=nz, n=n,
+               lap_coef=-0.5, beta=beta, gamma=tuple(gamma))
+    return out
 
 
 def stencil_to_csr(nx, ny, nz, h, lap_coef, diag):
