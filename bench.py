@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -60,13 +61,15 @@ def parse():
                          "solves, 1 timed) for the line's 'compare' entry")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--op", default=None, choices=["dense", "tc", "sliced", "small", "stencil", "gram"],
+    ap.add_argument("--op", default=None, choices=["dense", "tc", "sliced", "small", "stencil",
+                                                  "spectral", "spectral32", "gram"],
                     help="time one hot-path step alone (for ncu captures) instead of solves")
     ap.add_argument("--n", type=int, default=8192, help="order for --op")
     ap.add_argument("--cols", type=int, default=16, help="block columns for --op")
     ap.add_argument("--reps", type=int, default=3, help="launches for --op")
-    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3],
-                    help="1: dense n=8192 (default); 2: 64^3 stencil; 3: dense n=32768")
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3, 5],
+                    help="1: dense n=8192 (default); 2: 64^3 stencil; 3: dense n=32768; "
+                         "5: Fourier spectral BdG on 64^3 (Table 8, h0/4)")
     ap.add_argument("--serve", action="store_true",
                     help="serving workload: Poisson arrivals through lrep_server_*")
     ap.add_argument("--requests", type=int, default=1000)
@@ -172,6 +175,16 @@ def workload(precision, config=1):
                    "spectra": "k, m log-uniform [1e-2, 1e2], Haar Q1, Q2 (seed 3, device)",
                    "precision": precision, "window": "moving, s = 3",
                    "l2": "operator 17.2 GB resident, larger than L2 (no flush)"}
+    if config == 5:
+        p = synth.bdg_spectral(64)
+        p.update(nev=8, block=8, tol=1e-8, X0=p["phi"][:, None].copy())
+        return p, {"workload": "spectral-bdg-64^3-nev8-block8-null1-tol1e-8",
+                   "n": p["n"], "nev": 8, "block": 8, "tol": 1e-8, "nullspace": 1,
+                   "operator": "Fourier spectral -1/2 Lap_F + V + beta phi_s^2 - mu_s "
+                               "(+ 2 beta phi_s^2 for M), periodic (-8, 8)^3, beta = 100, "
+                               "gamma = (1, 1, 2), GPE ground state phi_s",
+                   "precision": precision, "window": "nb >= nev: Alg. 2 as printed",
+                   "l2": "block of 8 columns (16.8 MB) fits L2; operator is matrix-free"}
     p = synth.config(1)
     return p, {"workload": "dense-lrep-n8192-nev64-block16-null4-tol1e-10",
                "n": 8192, "nev": 64, "block": 16, "tol": 1e-10, "nullspace": 4,
@@ -188,7 +201,9 @@ def oracle_sample(p, sample_iters, full_iters):
     iterations on the same workload and scale to a full solve by the
     iteration count of a full solve."""
     from oracle import lrep_ref as R
-    if "dK" in p:
+    if "lengths" in p:
+        op = R.SpectralOp(p["nx"], p["ny"], p["nz"], p["lengths"], -0.5, p["dK"], p["dM"])
+    elif "dK" in p:
         op = R.StencilOp(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"], p["dM"])
     else:
         op = R.DenseOp(p["K"], p["M"])
@@ -291,6 +306,32 @@ def op_mode(args):
             torch.cuda.synchronize()
             times.append(ev[0].elapsed_time(ev[1]))
         work = {"flops": 9.0 * nn * c, "bytes": (16.0 * c + 8.0) * nn}
+        p.close()
+    elif args.op in ("spectral", "spectral32"):
+        N = args.n
+        nn = N ** 3
+        rng = np.random.default_rng(0)
+        dK, dM = rng.standard_normal(nn), rng.uniform(1.0, 2.0, nn)
+        p = lrep.Problem.spectral(N, N, N, (16.0, 16.0, 16.0), -0.5, dK, dM)
+        f32 = args.op == "spectral32"
+        if f32:
+            p.set_options(precision=lrep.PREC_MIXED_BF16X3)
+        X = torch.randn(c, nn, dtype=torch.float64, device="cuda", generator=g)
+        Y = torch.empty(c, nn, dtype=torch.float64, device="cuda")
+        for _ in range(args.reps):
+            ev[0].record()
+            p.apply(lrep.OP_K, X, Y, cg=f32)
+            ev[1].record()
+            torch.cuda.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]))
+        # conventional FFT flop count (5 N log2 N per complex transform of
+        # length N, two real lines per complex line, forward + inverse, the
+        # multiplier) plus the diagonal; bytes: X read and Y written once
+        # (algorithmic) and what the three per-axis passes move
+        lg = int(round(math.log2(N)))
+        work = {"flops": nn * c * (3.0 * (5.0 * lg + 1.0) + 2.0),
+                "bytes": (16.0 * c + 8.0) * nn, "pass_bytes": (64.0 * c + 8.0) * nn,
+                "grid": N, "transforms": "float32" if f32 else "float64"}
         p.close()
     elif args.op == "small":
         d = c
@@ -462,6 +503,9 @@ def main():
         prob = lrep.Problem.stencil(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"],
                                     p["dM"], stream=stream)
         args.no_e2e = True
+    elif args.config == 5:
+        prob = lrep.Problem.spectral(p["nx"], p["ny"], p["nz"], p["lengths"], -0.5, p["dK"],
+                                     p["dM"], stream=stream)
     else:
         Kd = p["K"] if not isinstance(p["K"], np.ndarray) else torch.from_numpy(p["K"]).to(dev)
         Md = p["M"] if not isinstance(p["M"], np.ndarray) else torch.from_numpy(p["M"]).to(dev)
@@ -523,13 +567,17 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6780.7)
     if args.config == 2:
         kname = "stencil_kernel (2.5-D)"
+    elif args.config == 5:
+        kname = ("spectral_axis_kernel<float> x 3 axes" if cg_dominant and
+                 (prec & lrep.PREC_MIXED_BF16X3) else "spectral_axis_kernel<double> x 3 axes")
     elif cg_dominant and (prec & lrep.PREC_MIXED_BF16X3):
         kname = "bf16x3_kernel (+ X split, split-K sum)"
     elif prec & lrep.PREC_FP64_SLICED:
         kname = "oz_gemm_kernel (+ X digit planes, split-K sum)"
     else:
         kname = "dense_apply_f64 (+ split-K reduce)"
-    hbm_bound = args.config == 2 or not kname.startswith("dense_apply_f64")
+    hbm_bound = args.config == 2 or not (kname.startswith("dense_apply_f64") or
+                                         kname.startswith("spectral_axis_kernel<double>"))
     roof = {"kernel": kname, "bound": "hbm" if hbm_bound else "alu",
             "achieved": flops_launch / avg_s / 1e12, "peak": FP64_PEAK_GFLOPS / 1e3,
             "unit": "TFLOP/s", "frac": (flops_launch / avg_s / 1e9) / FP64_PEAK_GFLOPS,
@@ -567,14 +615,19 @@ def main():
     # end to end through the public API from pinned host buffers
     e2e = None
     if not args.no_e2e:
-        Kh = torch.from_numpy(p["K"]).pin_memory()
-        Mh = torch.from_numpy(p["M"]).pin_memory()
+        spectral = args.config == 5
+        Kh = torch.from_numpy(p["dK" if spectral else "K"]).pin_memory()
+        Mh = torch.from_numpy(p["dM" if spectral else "M"]).pin_memory()
         times = []
         d2h = 0
         for s in range(args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            q = lrep.Problem.dense(Kh.numpy(), Mh.numpy(), stream=stream)
+            if spectral:
+                q = lrep.Problem.spectral(p["nx"], p["ny"], p["nz"], p["lengths"], -0.5,
+                                          Kh.numpy(), Mh.numpy(), stream=stream)
+            else:
+                q = lrep.Problem.dense(Kh.numpy(), Mh.numpy(), stream=stream)
             q.set_nullspace(p["X0"])
             q.set_options(precision=prec)
             st = q.solve(nev, nb, tol)
@@ -584,7 +637,7 @@ def main():
             times.append(time.perf_counter() - t0)
             d2h = lam.nbytes + X.nbytes + Y.nbytes
             q.close()
-        h2d = 2 * p["K"].nbytes + p["X0"].nbytes
+        h2d = Kh.numpy().nbytes + Mh.numpy().nbytes + p["X0"].nbytes
         e2e = {"value": world * nev / float(np.mean(times)), "unit": "eigenpairs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "seconds_per_step": float(np.mean(times))}

@@ -64,12 +64,13 @@ enum { LREP_FORM_AB = 0, LREP_FORM_KM = 1 };
  * lrep_set_mass_callback was called). */
 enum { LREP_OP_K = 0, LREP_OP_M = 1, LREP_OP_B = 2 };
 /* Arithmetic of the float64-accurate work and of the CG products (two
- * independent bits; bit 0 needs a dense operator).
+ * independent bits; bit 0 needs a dense or a spectral operator).
  * FP64: every product in float64 (FP64 FMA units).
  * MIXED_BF16X3 (bit 0): the inexact CG products of eq. block_GS use K, M
  *   split as hi + lo bfloat16 pairs (three bf16 tensor-core products, fp32
  *   accumulation); every product that enters H^ (eq. hat_H) and every
- *   residual (eq. tol) keeps float64 accuracy.
+ *   residual (eq. tol) keeps float64 accuracy.  Spectral operators: the CG
+ *   products run their transforms in float32 instead.
  * FP64_SLICED (bit 1): the float64-accurate dense products (and, without
  *   bit 0, the CG products too) and, for every operator kind, the large
  *   tall-skinny Grams and block updates of the solve run on the bf16 tensor
@@ -145,6 +146,24 @@ lrep_status lrep_create_stencil(lrep_problem* out, int32_t nx, int32_t ny,
                                 int32_t nz, double h, double lap_coef,
                                 const double* dK, const double* dM,
                                 int32_t mem, void* stream);
+
+/* Matrix-free Fourier spectral operator of the BdG example (Section 4,
+ * Example "large-scale dense matrix", eq. bdg_KM): a periodic box of side
+ * lengths L[0..2] sampled on an nx*ny*nz grid (index i + nx*(j + ny*k),
+ * spacing L_d / n_d), and
+ *   K x = lap_coef * Lap_F x + dK .* x,   M x = lap_coef * Lap_F x + dM .* x,
+ * where Lap_F multiplies Fourier mode m of axis d by -(2 pi m / L_d)^2 for
+ * the signed frequencies m in [-n_d/2, n_d/2) (the Nyquist mode included).
+ * nx, ny, nz: powers of two from 1 to 256 (1 = a flat axis).  With
+ * lap_coef = -1/2 and dK = V + beta phi^2 - mu, dM = dK + 2 beta phi^2 this
+ * is the BdG pair L_GP, L_GP + 2 beta |phi_s|^2 of eq. bdg_KM.  Products are
+ * one FFT pass per axis on the GPU (float64; float32 transforms for the CG
+ * products under LREP_PREC_MIXED_BF16X3).  dK, dM: float64[n], mem as for
+ * lrep_create_stencil. */
+lrep_status lrep_create_spectral(lrep_problem* out, int32_t nx, int32_t ny,
+                                 int32_t nz, const double* L, double lap_coef,
+                                 const double* dK, const double* dM,
+                                 int32_t mem, void* stream);
 
 /* User operator (the matrix-free interface of Section 1): fn is called
  * with device blocks; it must not retain the pointers. */

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblrep.so")
 
-SOURCES = ["k_blas.cu", "k_small.cu", "k_ops.cu", "k_tc.cu", "k_oz.cu", "mixed.cu",
+SOURCES = ["k_blas.cu", "k_small.cu", "k_ops.cu", "k_spectral.cu", "k_tc.cu", "k_oz.cu", "mixed.cu",
            "bosp.cu", "nullspace.cu", "capi.cu", "server.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -78,6 +78,13 @@ lrep_status apply_op(lrep_problem p, int which, int c, const double* X,
       e = stencil_apply_f64(o.nx, o.ny, o.nz, o.coef_h2, isK ? o.dK : o.dM, c,
                             X, ldx, Y, ldy, skip, p->stream);
       break;
+    case OP_SPECTRAL: {
+      if (isB) return p->fail(LREP_ERR_STATE, "spectral problems have no mass matrix");
+      const int dims[3] = {o.nx, o.ny, o.nz};
+      e = spectral_apply(false, dims, o.spec_scale, isK ? o.dK : o.dM, c, X, ldx, Y, ldy, skip,
+                         p->stream);
+      break;
+    }
     case OP_CALLBACK: {
       if (skip) {
         int h = 0;
@@ -360,7 +367,9 @@ struct Solver {
       LCK(oz_gram(n, A, B, G, ldg, ozws, ozws_bytes, p->op.tc_err, st));
       return LREP_OK;
     }
-    LCK(gram_f64(n, A, B, G, ldg, ws, ws_elems, st));
+    // row slabs capped to the planned workspace (shapes outside the plan,
+    // e.g. the 2 nb x 2 nb Gram of [W Z] on a long grid, use fewer slabs)
+    LCK(gram_f64_capped(n, A, B, G, ldg, ws, ws_elems, st));
     return LREP_OK;
   }
   lrep_status update(int c, double alpha, const Segs& A, const double* B,
@@ -415,6 +424,15 @@ struct Solver {
     } else if (o.kind == OP_STENCIL) {
       nnz = 7.0 * n;
       opbytes = 8.0 * n;  // the diagonal
+    } else if (o.kind == OP_SPECTRAL) {
+      // conventional FFT count: 5 N log2 N flops per complex line of N per
+      // transform, two real lines per complex line, forward + inverse, and
+      // the multiplier; as "nnz" per point (2 nnz c flops per product)
+      double per = 1.0;  // the diagonal
+      for (int a : {o.nx, o.ny, o.nz})
+        if (a > 1) per += 0.5 * (5.0 * spectral_log2(a) + 1.0);
+      nnz = per * n;
+      opbytes = 8.0 * n;
     } else if (o.kind == OP_CSR) {
       nnz = 7.0 * n;
       opbytes = 12.0 * nnz + 8.0 * (n + 1);

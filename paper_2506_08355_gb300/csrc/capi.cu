@@ -225,6 +225,48 @@ lrep_status lrep_create_csr(lrep_problem* out, int64_t n, int32_t form,
   return LREP_OK;
 }
 
+lrep_status lrep_create_spectral(lrep_problem* out, int32_t nx, int32_t ny, int32_t nz,
+                                 const double* L, double lap_coef, const double* dK,
+                                 const double* dM, int32_t mem, void* stream) {
+  const int dims[3] = {nx, ny, nz};
+  bool ok = out && L && dK && dM && valid_mem(mem) && std::isfinite(lap_coef);
+  for (int a = 0; ok && a < 3; ++a)
+    ok = (dims[a] == 1 || spectral_log2(dims[a]) > 0) && L[a] > 0.0 && std::isfinite(L[a]);
+  if (!ok) {
+    g_err = "lrep_create_spectral: invalid argument (grid sizes must be powers of two "
+            "from 1 to 256, box lengths positive)";
+    return LREP_ERR_ARG;
+  }
+  const int64_t n = (int64_t)nx * ny * nz;
+  lrep_problem p = new_problem(n, stream);
+  p->op.kind = OP_SPECTRAL;
+  p->op.nx = nx; p->op.ny = ny; p->op.nz = nz;
+  for (int a = 0; a < 3; ++a) {
+    const double k1 = 2.0 * M_PI / L[a];
+    p->op.spec_scale[a] = -lap_coef * k1 * k1 / (double)dims[a];
+  }
+  if (mem == LREP_MEM_DEVICE_BORROW) {
+    p->op.dK = const_cast<double*>(dK);
+    p->op.dM = const_cast<double*>(dM);
+  } else {
+    lrep_status s = copy_array(p, dK, n, &p->op.dK);
+    if (s == LREP_OK) s = copy_array(p, dM, n, &p->op.dM);
+    if (s != LREP_OK) {
+      g_err = p->err;
+      lrep_destroy(p);
+      return s;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) {
+    g_err = std::string("lrep_create_spectral: ") + cudaGetErrorString(e);
+    lrep_destroy(p);
+    return LREP_ERR_CUDA;
+  }
+  *out = p;
+  return LREP_OK;
+}
+
 lrep_status lrep_create_stencil(lrep_problem* out, int32_t nx, int32_t ny, int32_t nz,
                                 double h, double lap_coef, const double* dK,
                                 const double* dM, int32_t mem, void* stream) {
@@ -391,8 +433,9 @@ lrep_status lrep_set_options(lrep_problem p, const lrep_options* o) {
       !(o->discard_tol >= 0.0) || o->refresh_every < 1 || !(o->rebiorth_tol > 0.0) ||
       o->precision < LREP_PREC_FP64 || o->precision > LREP_PREC_MIXED_SLICED)
     return p->fail(LREP_ERR_ARG, "lrep_set_options: invalid value");
-  if ((o->precision & LREP_PREC_MIXED_BF16X3) && p->op.kind != OP_DENSE)
-    return p->fail(LREP_ERR_ARG, "the bf16 hi/lo CG operator needs a dense operator");
+  if ((o->precision & LREP_PREC_MIXED_BF16X3) && p->op.kind != OP_DENSE &&
+      p->op.kind != OP_SPECTRAL)
+    return p->fail(LREP_ERR_ARG, "mixed-precision CG products need a dense or spectral operator");
   const bool rebuild = (o->precision != p->opts.precision);
   p->opts = *o;
   if (rebuild) {

@@ -23,6 +23,16 @@ cudaError_t stencil_apply_f64(int nx, int ny, int nz, double coef_h2,
                               int64_t ldx, double* Y, int64_t ldy,
                               const int* skip, cudaStream_t st);
 
+// Fourier spectral operator on a periodic grid (k_spectral.cu):
+// Y = coef * Lap_F X + d .* X, with scale[ax] = -coef * (2 pi / L_ax)^2 / N_ax
+// and dims[ax] = N_ax powers of two <= 2^kSpectralMaxLog (1 = flat axis).
+// fp32: transforms in float (the inexact products of the block CG).
+constexpr int kSpectralMaxLog = 8;
+int spectral_log2(int N);
+cudaError_t spectral_apply(bool fp32, const int dims[3], const double scale[3],
+                           const double* d, int c, const double* X, int64_t ldx, double* Y,
+                           int64_t ldy, const int* skip, cudaStream_t st);
+
 // CSR SpMM: Y = A X.
 cudaError_t csr_apply_f64(int64_t n, const int64_t* rp, const int32_t* ci,
                           const double* v, int c, const double* X, int64_t ldx,

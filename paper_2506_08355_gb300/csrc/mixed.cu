@@ -1,7 +1,8 @@
 // Tensor-core operators of the dense K and M, built once per problem from
 // the float64 matrices according to opts.precision:
 //  * bit 0 (MIXED_BF16X3): hi + lo bfloat16 split for the inexact CG
-//    products of eq. block_GS (k_tc.cu);
+//    products of eq. block_GS (k_tc.cu); spectral operators need no split
+//    and run those products with float32 transforms (k_spectral.cu);
 //  * bit 1 (FP64_SLICED): seven bf16 digit planes for float64-accurate
 //    products by error-free slicing (k_oz.cu): every product that enters H^
 //    (eq. hat_H) and every residual (eq. tol), and the CG products when bit 0
@@ -24,14 +25,16 @@ bool want_oz(const lrep_problem p) { return (p->opts.precision & LREP_PREC_FP64_
 bool split_ready(lrep_problem p) {
   const Operator& o = p->op;
   const bool dense = o.kind == OP_DENSE;
-  return (p->opts.precision == LREP_PREC_FP64 || o.tc_err) && (!want_tc(p) || o.tcK) &&
+  return (p->opts.precision == LREP_PREC_FP64 || o.tc_err) &&
+         (!want_tc(p) || o.tcK || o.kind == OP_SPECTRAL) &&
          (!want_oz(p) || !dense || (o.ozK && (!o.hasB || o.ozB)));
 }
 
 size_t split_bytes(lrep_problem p) {
   const int64_t n = p->op.n;
   size_t b = 0;
-  if (want_tc(p)) b += (size_t)2 * 2 * 2 * tc_ld(n) * n;  // K, M x (hi, lo) bf16
+  if (want_tc(p) && p->op.kind == OP_DENSE)
+    b += (size_t)2 * 2 * 2 * tc_ld(n) * n;  // K, M x (hi, lo) bf16
   if (want_oz(p) && p->op.kind == OP_DENSE)               // K, M (B) x 7 digit planes
     b += (size_t)(p->op.hasB ? 3 : 2) * oz_operand_bytes(n);
   return b;
@@ -41,11 +44,11 @@ lrep_status build_split(lrep_problem p) {
   Operator& o = p->op;
   free_split(p);
   if (p->opts.precision == LREP_PREC_FP64) return LREP_OK;
-  if (want_tc(p) && o.kind != OP_DENSE)
-    return p->fail(LREP_ERR_ARG, "the bf16 hi/lo CG operator needs a dense operator");
+  if (want_tc(p) && o.kind != OP_DENSE && o.kind != OP_SPECTRAL)
+    return p->fail(LREP_ERR_ARG, "mixed-precision CG products need a dense or spectral operator");
   const int64_t n = o.n;
   const double* src[2] = {o.K, o.M};
-  if (want_tc(p)) {
+  if (want_tc(p) && o.kind == OP_DENSE) {
     const int64_t ldb = tc_ld(n);
     const size_t bytes = (size_t)ldb * n * 2;
     TcOperand* t[2] = {new TcOperand(), new TcOperand()};
@@ -142,6 +145,15 @@ lrep_status apply_op_cg(lrep_problem p, int which, int c, const double* X,
                         double* ws, size_t ws_elems) {
   if (!want_tc(p)) return apply_op(p, which, c, X, ldx, Y, ldy, skip, ws, ws_elems);
   const Operator& o = p->op;
+  if (o.kind == OP_SPECTRAL) {  // float32 transforms
+    const int dims[3] = {o.nx, o.ny, o.nz};
+    const cudaError_t e = spectral_apply(true, dims, o.spec_scale,
+                                         which == LREP_OP_K ? o.dK : o.dM, c, X, ldx, Y, ldy,
+                                         skip, p->stream);
+    if (e != cudaSuccess)
+      return p->fail(LREP_ERR_CUDA, std::string("spectral product: ") + cudaGetErrorString(e));
+    return LREP_OK;
+  }
   if (!o.tcK) return p->fail(LREP_ERR_STATE, "mixed precision operator split missing");
   cudaError_t e = tc_apply(which == LREP_OP_K ? *o.tcK : *o.tcM, o.n, c, X, ldx, Y, ldy, ws,
                            ws_elems * sizeof(double), o.tc_err, skip, p->stream);

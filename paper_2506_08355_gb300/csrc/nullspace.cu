@@ -152,7 +152,7 @@ struct NullFinder {
     return apply_op(p, LREP_OP_K, c, in, ld, out, ld, nullptr, ws, ws_elems);
   }
   lrep_status gram(const double* a, int ca, const double* b, int cb, double* g) {
-    NCK(gram_f64(n, seg1(a, ld, ca), seg1(b, ld, cb), g, ca, ws, ws_elems, st));
+    NCK(gram_f64_capped(n, seg1(a, ld, ca), seg1(b, ld, cb), g, ca, ws, ws_elems, st));
     return LREP_OK;
   }
   // out = a (n x k) * coef (k x c, ldc) (+ beta out)

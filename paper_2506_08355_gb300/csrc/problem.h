@@ -14,7 +14,7 @@ namespace lrep {
 struct TcOperand;
 struct OzOperand;
 
-enum OpKind { OP_DENSE = 0, OP_CSR = 1, OP_STENCIL = 2, OP_CALLBACK = 3 };
+enum OpKind { OP_DENSE = 0, OP_CSR = 1, OP_STENCIL = 2, OP_CALLBACK = 3, OP_SPECTRAL = 4 };
 
 // Device arena: one cudaMalloc, bump allocation, zero-filled on the stream
 // that uses it.
@@ -47,9 +47,10 @@ struct Operator {
   int64_t* rpM = nullptr;
   int32_t* ciM = nullptr;
   double* vM = nullptr;
-  // stencil
+  // stencil and spectral (grid nx*ny*nz, diagonals dK, dM)
   int nx = 0, ny = 0, nz = 0;
   double coef_h2 = 0.0;
+  double spec_scale[3] = {0.0, 0.0, 0.0};  // spectral: -coef (2 pi / L)^2 / N per axis
   double* dK = nullptr;
   double* dM = nullptr;
   // callback

@@ -50,6 +50,9 @@ EXPORTS = {
     "lrep_create_stencil": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
                                       C.c_int32, C.c_double, C.c_double, C.c_void_p,
                                       C.c_void_p, C.c_int32, C.c_void_p]),
+    "lrep_create_spectral": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
+                                       C.c_int32, C.c_void_p, C.c_double, C.c_void_p,
+                                       C.c_void_p, C.c_int32, C.c_void_p]),
     "lrep_create_operator": (C.c_int, [C.POINTER(C.c_void_p), C.c_int64, APPLY_FN,
                                        C.c_void_p, C.c_void_p]),
     "lrep_set_nullspace": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
@@ -252,6 +255,22 @@ class Problem:
         dm = np.ascontiguousarray(dM, dtype=np.float64)
         st = lib().lrep_create_stencil(C.byref(h), nx, ny, nz, h_grid, lap_coef,
                                        _ptr(dk), _ptr(dm), MEM_HOST, _stream(stream))
+        _check(st)
+        return cls(h, nx * ny * nz)
+
+    @classmethod
+    def spectral(cls, nx, ny, nz, lengths, lap_coef, dK, dM, stream=None):
+        """Periodic Fourier spectral operator (lrep_create_spectral):
+        K = lap_coef * Lap_F + diag(dK), M = lap_coef * Lap_F + diag(dM) on an
+        nx*ny*nz grid of a box with side lengths ``lengths``."""
+        h = C.c_void_p()
+        L = np.ascontiguousarray(lengths, dtype=np.float64)
+        if L.shape != (3,):
+            raise ValueError("lengths must hold three box lengths")
+        dk = np.ascontiguousarray(dK, dtype=np.float64)
+        dm = np.ascontiguousarray(dM, dtype=np.float64)
+        st = lib().lrep_create_spectral(C.byref(h), nx, ny, nz, _ptr(L), lap_coef,
+                                        _ptr(dk), _ptr(dm), MEM_HOST, _stream(stream))
         _check(st)
         return cls(h, nx * ny * nz)
 
