@@ -480,7 +480,8 @@ struct Solver {
                            const double* refa2, const double* refb2, int* kept,
                            const double* BAin = nullptr, const double* BBin = nullptr,
                            double* tBA = nullptr, double* tBB = nullptr,
-                           double* outBA = nullptr, double* outBB = nullptr) {
+                           double* outBA = nullptr, double* outBB = nullptr,
+                           bool near_identity = false) {
     const double tau = p->opts.discard_tol;
     *kept = 0;
     if (m <= 0) return LREP_OK;
@@ -490,7 +491,8 @@ struct Solver {
     Segs s = seg_push(seg1(Ain, ld, m), Bin, ld, m);
     Segs sb = bc ? seg_push(seg1(BAin, ld, m), BBin, ld, m) : s;
     LST(gram(s, sb, G2, ldg));
-    LCK(biorth_coef(m, G2, ldg, refa2, refb2, tau, cA, cB, dmax, cwork, cnt_d, st));
+    LCK(biorth_coef(m, G2, ldg, refa2, refb2, tau, cA, cB, dmax, cwork, cnt_d, st,
+                    near_identity));
     LCK(cudaMemcpyAsync(&h->cnt[0], cnt_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     LST(sync());
     const int k1 = h->cnt[0];
@@ -508,7 +510,8 @@ struct Solver {
     Segs s2 = seg_push(seg1(tA, ld, k1), tB, ld, k1);
     Segs s2b = bc ? seg_push(seg1(tBA, ld, k1), tBB, ld, k1) : s2;
     LST(gram(s2, s2b, G2, ldg));
-    LCK(biorth_coef(k1, G2, ldg, nullptr, nullptr, tau, cA2, cB2, dmax, cwork, cnt_d, st));
+    LCK(biorth_coef(k1, G2, ldg, nullptr, nullptr, tau, cA2, cB2, dmax, cwork, cnt_d, st,
+                    true));
     LCK(cudaMemcpyAsync(&h->cnt[0], cnt_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     LST(sync());
     const int k2 = h->cnt[0];
@@ -686,10 +689,11 @@ struct Solver {
     if (gen)
       LST(biorth_block(Ucur(), Vcur(), d, KUcur(), MVcur(), UX[t], UY[t], KX[t], MY[t],
                        UX[cur], UY[cur], KX[cur], MY[cur], nullptr, nullptr, &kept, BUcur(),
-                       BVcur(), BU[t], BV[t], BU[cur], BV[cur]));
+                       BVcur(), BU[t], BV[t], BU[cur], BV[cur], true));
     else
       LST(biorth_block(Ucur(), Vcur(), d, KUcur(), MVcur(), UX[t], UY[t], KX[t], MY[t],
-                       UX[cur], UY[cur], KX[cur], MY[cur], nullptr, nullptr, &kept));
+                       UX[cur], UY[cur], KX[cur], MY[cur], nullptr, nullptr, &kept, nullptr,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, true));
     if (kept == 0) return p->fail(LREP_ERR_BREAKDOWN, "re-biorthogonalisation lost every column");
     off = 0;
     d = kept;

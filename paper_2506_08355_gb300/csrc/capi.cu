@@ -753,7 +753,7 @@ lrep_status lrep_op_biorth(int64_t n, int32_t m, const double* W, const double* 
   Segs s2 = seg_push(seg1(tA, ld, k1), tB, ld, k1);
   if (e == cudaSuccess) e = gram_f64(n, s2, s2, G2, 2 * k1, gws, gws_elems, st);
   if (e == cudaSuccess)
-    e = biorth_coef(k1, G2, 2 * k1, nullptr, nullptr, tau, cA2, cB2, k1, cw, cnt, st);
+    e = biorth_coef(k1, G2, 2 * k1, nullptr, nullptr, tau, cA2, cB2, k1, cw, cnt, st, true);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(nullptr, "lrep_op_biorth", e);

@@ -975,6 +975,109 @@ biorth_coef_kernel(int m, const double* __restrict__ G2, int ld2,
   if (tid == 0) *count = kept;
 }
 
+// Alg. 1 in coefficient form through the LDU factorisation of S = W^T Z
+// without pivoting: the biorthogonal pair P = W A, Q = Z B with upper
+// triangular A, B and P^T Q = I is unique, and its pivots are the etas of
+// Alg. 1 (the Schur complement of the kept leading pairs).  Right-looking
+// elimination in shared memory, all threads on each rank-1 update of the
+// trailing block; a pair whose pivot fails the discard test is skipped (no
+// update), as Alg. 1 skips it.  Then A = L^-T D_a^-1 and B = U^-1 D_b^-1
+// over the kept indices (D_a D_b = D, D_b = sqrt|eta|), one column per warp
+// by column-oriented back substitution with the vector held in registers
+// (lane i % 32, slot i / 32).  For m <= kLuMaxM (S fits in shared memory)
+// and S close to the identity (see biorth_coef).
+constexpr int kLuMaxM = 160;
+constexpr int kLuSlots = (kLuMaxM + 31) / 32;
+
+__global__ void __launch_bounds__(1024)
+biorth_lu_kernel(int m, const double* __restrict__ G2, int ld2,
+                 const double* __restrict__ refw2, const double* __restrict__ refz2,
+                 double tau, double* __restrict__ A, double* __restrict__ B, int ldc,
+                 int* __restrict__ count) {
+  extern __shared__ double S[];  // m x m, S[i + j m]
+  __shared__ int keep[kLuMaxM], pos[kLuMaxM];
+  __shared__ int s_kept;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < m * m; e += nt) {
+    const int i = e % m, j = e / m;
+    S[e] = G2[i + (size_t)(m + j) * ld2];
+  }
+  __syncthreads();
+  for (int l = 0; l < m; ++l) {
+    if (tid == 0) {
+      const double eta = S[l + l * m];
+      const double rw = refw2 ? sqrt(refw2[l]) : sqrt(G2[l + (size_t)l * ld2]);
+      const double rz = refz2 ? sqrt(refz2[l]) : sqrt(G2[(m + l) + (size_t)(m + l) * ld2]);
+      keep[l] = isfinite(eta) && (fabs(eta) > tau * rw * rz);
+    }
+    __syncthreads();
+    if (keep[l]) {
+      const double inv = 1.0 / S[l + l * m];
+      const int r = m - l - 1;
+      for (int e = tid; e < r * r; e += nt) {
+        const int i = l + 1 + e % r, j = l + 1 + e / r;
+        S[i + j * m] = fma(-S[i + l * m] * inv, S[l + j * m], S[i + j * m]);
+      }
+      __syncthreads();
+      for (int e = tid; e < r; e += nt) {
+        S[(l + 1 + e) + l * m] *= inv;  // L(i, l)
+        S[l + (l + 1 + e) * m] *= inv;  // U(l, j)
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    int k = 0;
+    for (int l = 0; l < m; ++l) pos[l] = keep[l] ? k++ : -1;
+    s_kept = k;
+  }
+  __syncthreads();
+  const int kept = s_kept;
+  // columns past the kept ones are zero
+  for (int e = tid; e < m * (m - kept); e += nt) {
+    const int i = e % m, j = kept + e / m;
+    A[i + (size_t)j * ldc] = 0.0;
+    B[i + (size_t)j * ldc] = 0.0;
+  }
+  // task t < m: A column of index t; t >= m: B column of index t - m
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  for (int t = warp; t < 2 * m; t += nw) {
+    const bool isB = t >= m;
+    const int lk = isB ? t - m : t;
+    if (!keep[lk]) continue;
+    double xv[kLuSlots];
+#pragma unroll
+    for (int sl = 0; sl < kLuSlots; ++sl) xv[sl] = (sl * 32 + lane == lk) ? 1.0 : 0.0;
+    for (int j = lk; j > 0; --j) {
+      if (!keep[j]) continue;
+      double own = 0.0;
+#pragma unroll
+      for (int sl = 0; sl < kLuSlots; ++sl)
+        if (sl == (j >> 5)) own = xv[sl];
+      const double xj = __shfl_sync(0xffffffffu, own, j & 31);
+      // L^T x = e: x_i -= L(j, i) x_j;  U y = e: y_i -= U(i, j) y_j  (i < j)
+#pragma unroll
+      for (int sl = 0; sl < kLuSlots; ++sl) {
+        const int i = sl * 32 + lane;
+        if (i < j && keep[i]) {
+          const double c = isB ? S[i + j * m] : S[j + i * m];
+          xv[sl] = fma(-c, xj, xv[sl]);
+        }
+      }
+    }
+    const double eta = S[lk + lk * m];
+    const double root = sqrt(fabs(eta));
+    const double scl = isB ? root : (eta > 0.0 ? root : -root);
+    double* out = (isB ? B : A) + (size_t)pos[lk] * ldc;
+#pragma unroll
+    for (int sl = 0; sl < kLuSlots; ++sl) {
+      const int i = sl * 32 + lane;
+      if (i < m) out[i] = (i <= lk && keep[i]) ? xv[sl] / scl : 0.0;
+    }
+  }
+  if (tid == 0) *count = kept;
+}
+
 __global__ void biorth_error_kernel(int d, const double* __restrict__ S, int lds,
                                     double* __restrict__ out) {
   __shared__ double red[32];
@@ -1061,13 +1164,31 @@ size_t biorth_coef_work_elems(int m) { return (size_t)2 * m * m; }
 
 cudaError_t biorth_coef(int m, const double* G2, int ld2, const double* ref_w2,
                         const double* ref_z2, double tau, double* A, double* B,
-                        int ldc, double* work, int* count, cudaStream_t st) {
+                        int ldc, double* work, int* count, cudaStream_t st,
+                        bool near_identity) {
   if (m <= 0) return cudaSuccess;
   constexpr int kCoefDyn = 200 * 1024;
   static const cudaError_t attr = cudaFuncSetAttribute(
       biorth_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCoefDyn);
   if (attr != cudaSuccess) return attr;
   if ((size_t)3 * m * sizeof(double) > (size_t)kCoefDyn) return cudaErrorInvalidValue;
+  // The LU form serves the passes over bases that are already nearly
+  // biorthogonal (S close to I: the safeguard's pass over U, V and every
+  // second pass).  A first pass over new directions (the W, Z of eq.
+  // update_W/Z, a random start block) keeps the MGS coefficient form, which
+  // takes every projection coefficient afresh from the original Gram; the
+  // Schur-complement updates of the LU form accumulate rounding in the
+  // trailing block, and on ill-conditioned W^T Z that stalled a 64^3 stencil
+  // solve at residual 1.4e-8.
+  if (m <= kLuMaxM && near_identity) {
+    constexpr int kLuDyn = kLuMaxM * kLuMaxM * (int)sizeof(double);
+    static const cudaError_t lu_attr = cudaFuncSetAttribute(
+        biorth_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLuDyn);
+    if (lu_attr != cudaSuccess) return lu_attr;
+    biorth_lu_kernel<<<1, 1024, (size_t)m * m * sizeof(double), st>>>(
+        m, G2, ld2, ref_w2, ref_z2, tau, A, B, ldc, count); LREP_COUNT_LAUNCH();
+    return cudaGetLastError();
+  }
   biorth_coef_kernel<<<1, 512, kCoefDyn, st>>>(m, G2, ld2, ref_w2, ref_z2, tau, A, B,
                                                ldc, work, count, kCoefDyn); LREP_COUNT_LAUNCH();
   return cudaGetLastError();

@@ -162,11 +162,14 @@ cudaError_t small_pq(const PqJob& job, cudaStream_t st);
 // Alg. 1 in coefficient space from the Gram G2 = [W Z]^T [W Z] (2m x 2m,
 // ld2): writes A, B (m x m, ldc; first `count` columns valid) so that
 // P = W A, Q = Z B are biorthogonal.  ref_w, ref_z: entering norms
-// (nullptr: sqrt(diag)).
+// (nullptr: sqrt(diag)).  near_identity: W^T Z is known to be close to I
+// (a pass over an already biorthogonal basis), which allows the parallel
+// LU form.
 size_t biorth_coef_work_elems(int m);
 cudaError_t biorth_coef(int m, const double* G2, int ld2, const double* ref_w2,
                         const double* ref_z2, double tau, double* A, double* B,
-                        int ldc, double* work, int* count, cudaStream_t st);
+                        int ldc, double* work, int* count, cudaStream_t st,
+                        bool near_identity = false);
 
 // max |S - I| of a d x d matrix into *out (one CTA)
 cudaError_t biorth_error(int d, const double* S, int lds, double* out, cudaStream_t st);
