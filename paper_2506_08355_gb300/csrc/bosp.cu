@@ -362,8 +362,24 @@ struct Solver {
   // float64-accurate products below this many flops stay on the FP64 units
   // (the sliced form costs ~5 launches)
   static constexpr double kSlicedMinFlops = 1.6e7;
+  // The sliced route moves a fixed number of passes over its inputs and
+  // digit planes (contraction padded to 64 for updates); the FP64 kernels
+  // cost 2 flops per multiply-add at ~0.9 TF/s.  Grams take the sliced route
+  // unless one side has fewer than 8 columns (a rank-few projection: the
+  // digit passes over the long side then cost more than the FP64 product);
+  // updates only where
+  // the modelled sliced time (at ~5 TB/s) is below half the FP64 time, so
+  // thin ones (k = 24, c = 8, say) stay FP64.
+  static bool sliced_gram_pays(int a, int b) { return a >= 8 && b >= 8; }
+  static bool sliced_update_pays(int k, int c) {
+    const double ldk = (k + 63) / 64 * 64;
+    const double t_sl = (8.0 * k + 28.0 * ldk + 24.0 * c) / 5e12;
+    const double t_fp = 2.0 * k * c / 0.9e12;
+    return t_sl < 0.5 * t_fp;
+  }
   lrep_status gram(const Segs& A, const Segs& B, double* G, int64_t ldg) {
-    if (oz && 2.0 * n * A.total() * B.total() >= kSlicedMinFlops) {
+    if (oz && 2.0 * n * A.total() * B.total() >= kSlicedMinFlops &&
+        sliced_gram_pays(A.total(), B.total())) {
       LCK(oz_gram(n, A, B, G, ldg, ozws, ozws_bytes, p->op.tc_err, st));
       return LREP_OK;
     }
@@ -374,7 +390,8 @@ struct Solver {
   }
   lrep_status update(int c, double alpha, const Segs& A, const double* B,
                      int64_t ldb, double beta, double* Cm) {
-    if (oz && beta != 0.0 && 2.0 * n * A.total() * c >= kSlicedMinFlops) {
+    if (oz && beta != 0.0 && 2.0 * n * A.total() * c >= kSlicedMinFlops &&
+        sliced_update_pays(A.total(), c)) {
       LCK(oz_update(n, A.total(), c, alpha, A, B, ldb, beta, Cm, ld, ozws, ozws_bytes,
                     p->op.tc_err, st));
       return LREP_OK;

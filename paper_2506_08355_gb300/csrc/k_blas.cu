@@ -266,34 +266,37 @@ cudaError_t gram_f64_capped(int64_t n, const Segs& A, const Segs& B, double* G,
 
 // =====================================================================
 // Block update C = alpha C + beta A B, A n x k (segmented), B k x c.
-// CTA = 64 rows x 32 columns; 256 threads: row = t % 64, 8 columns each.
+// CTA = UM rows x UN columns with UM * UN = 2048; 256 threads, each one row
+// and 8 columns; UN = 8, 16 or 32 follows c, so thin updates (c = 8 in a
+// block of 8) do no work on padding columns.
 // =====================================================================
 namespace {
-constexpr int UM = 64, UN = 32, UK = 16;
+constexpr int UK = 16;
 
+template <int UN>
 __global__ void __launch_bounds__(256)
 update_kernel(int64_t n, int c, int k, double alpha, Segs A,
               const double* __restrict__ B, int64_t ldb, double beta,
               double* __restrict__ C, int64_t ldc) {
+  constexpr int UM = 2048 / UN;
+  constexpr int G = UN / 8;  // column groups of 8
   __shared__ double As[UK][UM];
   __shared__ double Bs[UK][UN + 1];
   const int t = threadIdx.x;
   const int64_t i0 = (int64_t)blockIdx.x * UM;
   const int j0 = blockIdx.y * UN;
-  const int r = t & 63, g = t >> 6;
+  const int r = t % UM, g = t / UM;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int k0 = 0; k0 < k; k0 += UK) {
 #pragma unroll
     for (int s = 0; s < (UK * UM) / 256; ++s) {
       const int e = t + s * 256;
-      const int rr = e & 63, kk = e >> 6;
+      const int rr = e % UM, kk = e / UM;
       const int64_t row = i0 + rr;
       const int col = k0 + kk;
       As[kk][rr] = (row < n && col < k) ? A.col(col)[row] : 0.0;
     }
-#pragma unroll
-    for (int s = 0; s < (UK * UN) / 256; ++s) {
-      const int e = t + s * 256;
+    for (int e = t; e < UK * UN; e += 256) {
       const int kk = e % UK, jj = e / UK;
       const int col = k0 + kk, j = j0 + jj;
       Bs[kk][jj] = (col < k && j < c) ? B[col + (int64_t)j * ldb] : 0.0;
@@ -307,6 +310,7 @@ update_kernel(int64_t n, int c, int k, double alpha, Segs A,
     }
     __syncthreads();
   }
+  static_assert(G * UM == 256, "one row and 8 columns per thread");
   const int64_t row = i0 + r;
   if (row >= n) return;
 #pragma unroll
@@ -318,6 +322,15 @@ update_kernel(int64_t n, int c, int k, double alpha, Segs A,
     *cp = (alpha == 0.0) ? v : fma(alpha, *cp, v);
   }
 }
+
+template <int UN>
+void launch_update(int64_t n, int c, int k, double alpha, const Segs& A, const double* B,
+                   int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st) {
+  constexpr int UM = 2048 / UN;
+  dim3 grid((unsigned)((n + UM - 1) / UM), (unsigned)((c + UN - 1) / UN));
+  update_kernel<UN><<<grid, 256, 0, st>>>(n, c, k, alpha, A, B, ldb, beta, C, ldc);
+  LREP_COUNT_LAUNCH();
+}
 }  // namespace
 
 cudaError_t update_f64(int64_t n, int c, double alpha, const Segs& A,
@@ -325,8 +338,12 @@ cudaError_t update_f64(int64_t n, int c, double alpha, const Segs& A,
                        int64_t ldc, cudaStream_t st) {
   if (n <= 0 || c <= 0) return cudaSuccess;
   const int k = A.total();
-  dim3 grid((unsigned)((n + UM - 1) / UM), (unsigned)((c + UN - 1) / UN));
-  update_kernel<<<grid, 256, 0, st>>>(n, c, k, alpha, A, B, ldb, beta, C, ldc); LREP_COUNT_LAUNCH();
+  if (c <= 8)
+    launch_update<8>(n, c, k, alpha, A, B, ldb, beta, C, ldc, st);
+  else if (c <= 16)
+    launch_update<16>(n, c, k, alpha, A, B, ldb, beta, C, ldc, st);
+  else
+    launch_update<32>(n, c, k, alpha, A, B, ldb, beta, C, ldc, st);
   return cudaGetLastError();
 }
 
