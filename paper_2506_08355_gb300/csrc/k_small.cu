@@ -216,6 +216,7 @@ __device__ bool small_phase1(const SmallJob& J, const SmallMats& mm, int* sweeps
   int gsz = 32;
   while (gsz > 16 && npairs > nt / gsz) gsz >>= 1;
   const int ngroups = nt / gsz, gid = tid / gsz, glane = tid % gsz;
+  const int warp_gid0 = (tid >> 5) * (32 / gsz);  // first group of this warp
   int sweeps = 0;
   for (int sweep = 0; sweep < 30; ++sweep) {
     ++sweeps;
@@ -223,14 +224,24 @@ __device__ bool small_phase1(const SmallJob& J, const SmallMats& mm, int* sweeps
     __syncthreads();
     for (int r = 0; r < m; ++r) {
       // the pairs of the round in lane groups of gsz lanes (16 or 32: one
-      // group per pair when they fit); every lane runs the same trip count
-      // (inactive groups idle through the shuffles)
+      // group per pair when they fit); every lane of a working warp runs the
+      // same trip count (inactive groups idle through the shuffles)
       for (int base = 0; base < npairs; base += ngroups) {
+        // warps whose groups all lie past the last pair skip the round (the
+        // shuffles below stay within a warp); the kernel is issue-bound
+        if (base + warp_gid0 >= npairs) continue;
         const int p = base + gid;
         int a = 0, b = 0;
         if (p < npairs) {
-          if (p == 0) { a = r; b = m; }
-          else { a = (r + p) % m; b = (r - p + m) % m; }
+          if (p == 0) {
+            a = r;
+            b = m;
+          } else {  // (r + p) mod m and (r - p) mod m for 0 <= r < m, 0 < p < m
+            a = r + p;
+            if (a >= m) a -= m;
+            b = r - p;
+            if (b < 0) b += m;
+          }
           if (a > b) { const int t = a; a = b; b = t; }
         }
         const bool live = p < npairs && b < d;
