@@ -158,8 +158,11 @@ lrep_status lrep_create_stencil(lrep_problem* out, int32_t nx, int32_t ny,
  * lap_coef = -1/2 and dK = V + beta phi^2 - mu, dM = dK + 2 beta phi^2 this
  * is the BdG pair L_GP, L_GP + 2 beta |phi_s|^2 of eq. bdg_KM.  Products are
  * one FFT pass per axis on the GPU (float64; float32 transforms for the CG
- * products under LREP_PREC_MIXED_BF16X3).  dK, dM: float64[n], mem as for
- * lrep_create_stencil. */
+ * products under LREP_PREC_MIXED_BF16X3).  L: host float64[3].  dK, dM:
+ * float64[n], mem as for lrep_create_stencil (copied unless borrowed; a
+ * borrowed array must outlive the problem).  LREP_ERR_ARG when a grid size
+ * is not a power of two in 1..256, a length is not positive and finite, or
+ * a pointer is NULL. */
 lrep_status lrep_create_spectral(lrep_problem* out, int32_t nx, int32_t ny,
                                  int32_t nz, const double* L, double lap_coef,
                                  const double* dK, const double* dM,
