@@ -132,3 +132,20 @@ def test_bdg_spectral_table8_first_column():
     np.testing.assert_allclose(lam, tab, rtol=0, atol=2e-10)
     # the x <-> y symmetry makes lambda_1 = lambda_2 exactly
     assert abs(lam[1] - lam[0]) < 1e-12
+
+
+def test_bosp_on_spectral_operator_vs_definition():
+    """The literal Alg. 2 of the oracle on the spectral operator (8^3 grid of
+    (-4, 4)^3, beta = 10, deflated by phi_s) agrees with the definition
+    route."""
+    p = synth.bdg_spectral(8, 8, 8, box=(8.0, 8.0, 8.0), beta=10.0)
+    op = R.SpectralOp(8, 8, 8, p["lengths"], -0.5, p["dK"], p["dM"])
+    K = op.apply("K", np.eye(512))
+    M = op.apply("M", np.eye(512))
+    K, M = 0.5 * (K + K.T), 0.5 * (M + M.T)
+    kap, Vk = np.linalg.eigh(K)
+    FK = Vk[:, 1:] * np.sqrt(kap[1:])[None, :]
+    ref = R.lrep_definition_values(FK, np.linalg.cholesky(M), 6)
+    out = R.bosp(op, 6, 6, 1e-10, X0=p["phi"][:, None])
+    np.testing.assert_allclose(out["lam"], ref, rtol=1e-10)
+    assert R.residuals(op, out["X"], out["Y"], out["lam"]).max() < 1e-10
