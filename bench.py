@@ -62,14 +62,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--op", default=None, choices=["dense", "tc", "sliced", "small", "stencil",
-                                                  "spectral", "spectral32", "gram"],
+                                                  "spectral", "spectral32", "gram", "nullspace"],
                     help="time one hot-path step alone (for ncu captures) instead of solves")
     ap.add_argument("--n", type=int, default=8192, help="order for --op")
     ap.add_argument("--cols", type=int, default=16, help="block columns for --op")
     ap.add_argument("--reps", type=int, default=3, help="launches for --op")
-    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3, 5],
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 3, 5, 6],
                     help="1: dense n=8192 (default); 2: 64^3 stencil; 3: dense n=32768; "
-                         "5: Fourier spectral BdG on 64^3 (Table 8, h0/4)")
+                         "5: Fourier spectral BdG on 64^3 (Table 8, h0/4); 6: the n=8192 "
+                         "workload as a generalized LREP with an SPD mass matrix B")
     ap.add_argument("--serve", action="store_true",
                     help="serving workload: Poisson arrivals through lrep_server_*")
     ap.add_argument("--requests", type=int, default=1000)
@@ -175,6 +176,17 @@ def workload(precision, config=1):
                    "spectra": "k, m log-uniform [1e-2, 1e2], Haar Q1, Q2 (seed 3, device)",
                    "precision": precision, "window": "moving, s = 3",
                    "l2": "operator 17.2 GB resident, larger than L2 (no flush)"}
+    if config == 6:
+        p = dict(synth.config(1))
+        b = synth.haar_dense_device(8192, seed=11, k_range=(0.5, 2.0), m_range=(0.5, 2.0))
+        p["B"] = b["K"]
+        del b
+        return p, {"workload": "generalized-dense-lrep-n8192-nev64-block16-null4-tol1e-10",
+                   "n": 8192, "nev": 64, "block": 16, "tol": 1e-10, "nullspace": 4,
+                   "spectra": "k, m ~ U[0.5, 10], Haar Q1, Q2 (seed 1); mass matrix "
+                              "B = Q3 diag(b) Q3^T, b ~ U[0.5, 2] (seed 11, device)",
+                   "precision": precision, "window": "moving, s = 3",
+                   "l2": "operator K, M, B 1.61 GB resident, larger than L2 (no flush)"}
     if config == 5:
         p = synth.bdg_spectral(64)
         p.update(nev=8, block=8, tol=1e-8, X0=p["phi"][:, None].copy())
@@ -203,6 +215,9 @@ def oracle_sample(p, sample_iters, full_iters):
     from oracle import lrep_ref as R
     if "lengths" in p:
         op = R.SpectralOp(p["nx"], p["ny"], p["nz"], p["lengths"], -0.5, p["dK"], p["dM"])
+    elif "B" in p:
+        Bh = p["B"] if isinstance(p["B"], np.ndarray) else p["B"].cpu().numpy()
+        op = R.DenseOp(p["K"], p["M"], Bh)
     elif "dK" in p:
         op = R.StencilOp(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"], p["dM"])
     else:
@@ -333,6 +348,29 @@ def op_mode(args):
                 "bytes": (16.0 * c + 8.0) * nn, "pass_bytes": (64.0 * c + 8.0) * nn,
                 "grid": N, "transforms": "float32" if f32 else "float64"}
         p.close()
+    elif args.op == "nullspace":
+        # nullspace discovery (LOBPCG on K) on the n = 8192 workload with its
+        # 4-dimensional N(K); the call synchronises, so host-timed
+        from paper_2506_08355_gb300 import synth
+        p = synth.config(1)
+        Kd = torch.from_numpy(p["K"]).cuda()
+        Md = torch.from_numpy(p["M"]).cuda()
+        prob = lrep.Problem.dense(Kd, Md, borrow=True)
+        for _ in range(args.reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            X0, its = prob.find_nullspace(r_max=8, tol=1e-10)
+            torch.cuda.synchronize()
+            times.append(1e3 * (time.perf_counter() - t0))
+        X0d = torch.from_numpy(X0).cuda()
+        knorm = float((Kd @ X0d).abs().max())
+        Pt = p["X0"] @ np.linalg.pinv(p["X0"])
+        work = {"flops": 0.0, "bytes": 0.0, "r": int(X0.shape[1]), "iterations": int(its),
+                "max_abs_K_X0": knorm,
+                "projector_err": float(np.abs(X0 @ X0.T - Pt).max()), "r_max": 8,
+                "tol": 1e-10}
+        n = 8192
+        prob.close()
     elif args.op == "small":
         d = c
         A = torch.randn(d, d, dtype=torch.float64, device="cuda", generator=g)
@@ -510,6 +548,9 @@ def main():
         Kd = p["K"] if not isinstance(p["K"], np.ndarray) else torch.from_numpy(p["K"]).to(dev)
         Md = p["M"] if not isinstance(p["M"], np.ndarray) else torch.from_numpy(p["M"]).to(dev)
         prob = lrep.Problem.dense(Kd, Md, borrow=True, stream=stream)
+        if args.config == 6:
+            prob.set_mass(p["B"], borrow=True)
+            args.no_e2e = True
     if args.config == 3:
         args.no_e2e = True
         args.no_cpu = True
