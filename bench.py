@@ -3,7 +3,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision fp64|mixed|sliced|mixed-sliced] [--compare P]
-                    [--config 1|2|3] [--op ...] [--serve ...]
+                    [--config 1|2|3|5|6] [--op ...] [--serve ...]
 
 One step is one complete solve (Alg. 2 with the moving window) of the dense
 n = 8192 workload: K, M built from chosen spectra with Haar bases, k and m
@@ -23,6 +23,13 @@ Also reported: the dominant kernel's roofline (timed per launch with CUDA
 events on the solver's stream), an end-to-end figure through the C ABI from
 pinned host buffers, the CPU oracle as a baseline, and the SM clocks sampled
 during the timed region.
+
+Other workloads (same JSON line): --config 2, the 64^3 BdG-like stencil;
+--config 3, the dense n = 32768 log-uniform problem; --config 5, the Fourier
+spectral BdG problem on 64^3 (Table 8, h = h0/4, tol 1e-8); --config 6, the
+n = 8192 workload as a generalized LREP with an SPD mass matrix.  --op times
+one hot-path step alone (products, the small LREP, Grams, nullspace
+discovery) for kernel captures; --serve runs the request-serving trace.
 """
 from __future__ import annotations
 
