@@ -242,7 +242,7 @@ lrep_status lrep_create_spectral(lrep_problem* out, int32_t nx, int32_t ny, int3
   p->op.kind = OP_SPECTRAL;
   p->op.nx = nx; p->op.ny = ny; p->op.nz = nz;
   for (int a = 0; a < 3; ++a) {
-    const double k1 = 2.0 * M_PI / L[a];
+    const double k1 = 2.0 * 3.14159265358979323846 / L[a];  // 2 pi / L
     p->op.spec_scale[a] = -lap_coef * k1 * k1 / (double)dims[a];
   }
   if (mem == LREP_MEM_DEVICE_BORROW) {
