@@ -367,6 +367,38 @@ oz_coldigits_kernel(Segs src, int64_t n, int ncols, int64_t ld,
     write_digits((live && k < n) ? col[k] : 0ull, e, out + k, sstride);
 }
 
+// Both passes in one CTA per column when a column fits one chunk (ld <=
+// kChunk): the block's maximum, then the digits (a second read that hits
+// the cache).  Same exponents and digits as oz_colmax_kernel followed by
+// oz_coldigits_kernel.
+__global__ void __launch_bounds__(256)
+oz_colslice_kernel(Segs src, int64_t n, int ncols, int64_t ld, uint16_t* __restrict__ dst,
+                   int64_t sstride, int* __restrict__ expo) {
+  const int j = blockIdx.y;
+  const bool live = j < ncols;
+  const uint64_t* col = live ? (const uint64_t*)src.col(j) : nullptr;
+  uint64_t m = 0;
+  if (live)
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+      const uint64_t a = col[k] & kAbs;
+      if (a < kInf && a > m) m = a;
+    }
+  __shared__ uint64_t red[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t > m ? t : m;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+  const int e = live ? scale_exponent(m) : 0;
+  if (threadIdx.x == 0 && expo) expo[j] = e;
+  uint16_t* out = dst + (int64_t)j * ld;
+  for (int64_t k = threadIdx.x; k < ld; k += blockDim.x)
+    write_digits((live && k < n) ? col[k] : 0ull, e, out + k, sstride);
+}
+
 // Transposing slicer for a tall left operand: rows r of a segmented n x k
 // block become digit rows dst[s * sstride + r * ldk + kk] (per-row scale
 // expo[r]); rows n..gridDim.x*kRows-1 and entries k..ldk-1 zero.
@@ -473,6 +505,12 @@ unsigned grid1(int64_t tot) {
 // group of width C, into xs / tau (maxbits: C words of scratch)
 cudaError_t slice_columns(const Segs& X, int64_t k, int c, int C, int64_t ldk, uint16_t* xs,
                           int* tau, unsigned long long* maxbits, cudaStream_t st) {
+  if (ldk <= kChunk) {  // one CTA per column: both passes in one launch
+    oz_colslice_kernel<<<dim3(1, (unsigned)C), 256, 0, st>>>(X, k, c, ldk, xs,
+                                                            (int64_t)C * ldk, tau);
+    LREP_COUNT_LAUNCH();
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long) * C, st);
   if (e != cudaSuccess) return e;
   const unsigned chunks_n = (unsigned)std::max<int64_t>(1, (k + kChunk - 1) / kChunk);
