@@ -64,7 +64,8 @@ import numpy as np
 
 class DenseOp:
     """K, M (and optionally the SPD B of the generalized LREP, Remark on
-    the generalized LREP) stored as dense symmetric matrices."""
+    the generalized LREP) stored as dense symmetric matrices.
+    Parity: the product is numpy's matmul (a library primitive)."""
 
     def __init__(self, K, M, B=None):
         self.K = np.asarray(K, dtype=np.float64)
@@ -82,6 +83,8 @@ class StencilOp:
     """lap_coef * Lap_h + diag(d) on an nx*ny*nz grid, zero ghost values.
 
     Lap_h x = sum_d (x[+e_d] + x[-e_d] - 2 x) / h^2, index i + nx*(j+ny*k).
+    Parity: pinned (separable spectrum = Kronecker sum of the closed-form
+    1-D tridiagonal eigenvalues; K phi = 0 for the Gaussian workload).
     """
 
     def __init__(self, nx, ny, nz, h, lap_coef, dK, dM):
@@ -147,7 +150,9 @@ class SpectralOp:
 
 
 class CsrOp:
-    """K, M given as CSR triples (rowptr, colind, values)."""
+    """K, M given as CSR triples (rowptr, colind, values).
+    Parity: pinned (equal to the pinned stencil operator through an
+    independent stencil-to-CSR conversion)."""
 
     def __init__(self, n, csrK, csrM):
         self.n = n
@@ -209,6 +214,8 @@ def lrep_definition_gen(K, M, Bm, nev, r=0):
     with x' = L^T x, y' = L^T y (K' x' = L^-1 K x = lam L^-1 B y = lam y',
     and x'^T y' = x^T B y), solved by ``lrep_definition``.
     Returns (lam ascending, X, Y) with X, Y of shape n x nev.
+    Parity: pinned (B = beta I scales the eigenvalues by 1/beta; the
+    eigenvalues of the pencil; K x = lam B y, M y = lam B x, X^T B Y = I).
     """
     L = np.linalg.cholesky(np.asarray(Bm, dtype=np.float64))
     Kp = np.linalg.solve(L, np.linalg.solve(L, np.asarray(K, dtype=np.float64)).T)
@@ -231,7 +238,8 @@ def lrep_definition_values(FK, FM, nev, r=0):
 
 
 def fix_sign(X, Y):
-    """Scale pair columns by +-1 so that the largest-|.| entry of x is > 0."""
+    """Scale pair columns by +-1 so that the largest-|.| entry of x is > 0
+    (a sign convention; both sides apply the same one)."""
     X = np.array(X, dtype=np.float64, copy=True)
     Y = np.array(Y, dtype=np.float64, copy=True)
     for i in range(X.shape[1]):
@@ -295,6 +303,7 @@ def cgs_biorth(X, Y):
 
     Coefficients use the original x, y: r_j = q_j^T x, s_j = p_j^T y.
     Test-only comparator for Table 1 (no discard).
+    Parity: pinned (Table 1 losses within 10x).
     """
     X = np.asarray(X, dtype=np.float64)
     Y = np.asarray(Y, dtype=np.float64)
@@ -350,7 +359,9 @@ def small_lrep(Khat, Mhat):
 def cg(apply_fn, B, tol, maxit):
     """Plain CG per column from a zero start (reading of 'tolerance 1e-2,
     at most 20 iterations', text after eq. block_GS).  Columns stop
-    independently when ||r|| <= tol ||b||.  Returns (X, iterations run)."""
+    independently when ||r|| <= tol ||b||.  Returns (X, iterations run).
+    Parity: pinned (reaches ||r|| <= tol ||b|| on an SPD system; exact
+    solution within the tolerance)."""
     B = np.asarray(B, dtype=np.float64)
     X = np.zeros_like(B)
     R = B.copy()
@@ -378,7 +389,8 @@ def residuals(op, X, Y, lam, KX=None, MY=None, BX=None, BY=None):
     """eq. tol: ||H xi - lam xi|| / ((1 + lam) ||xi||), xi = [y; x]; for the
     generalized LREP H xi - lam diag(B, B) xi.
 
-    KX, MY (BX, BY) may be passed when already formed (K U X^ = (K U) X^)."""
+    KX, MY (BX, BY) may be passed when already formed (K U X^ = (K U) X^).
+    Parity: pinned (hand-computed values)."""
     KX = op.apply("K", X) if KX is None else KX
     MY = op.apply("M", Y) if MY is None else MY
     gen = getattr(op, "B", None) is not None
@@ -396,7 +408,9 @@ def nullspace_definition(K, tol):
     definition: the eigenvectors of K whose eigenvalues are at most
     tol * ||K||_2 (the pre-step of the Remark on the numerical computation
     of the generalized nullspace, which leaves the symmetric eigensolver
-    open).  Returns X0 (n x r) and all eigenvalues ascending."""
+    open).  Returns X0 (n x r) and all eigenvalues ascending.
+    Parity: pinned (a chosen kernel is recovered, a near-kernel above the
+    threshold is not, the zero matrix)."""
     w, V = np.linalg.eigh(np.asarray(K, dtype=np.float64))
     nrm = np.abs(w).max() if w.size else 0.0
     keep = w <= tol * nrm
@@ -410,6 +424,7 @@ def setup_nullspace(op, X0, Y0=None, cg_tol=1e-14, cg_maxit=50000):
     nullspace": CG on the SPD system) unless given; then with
     X0^T Y0 = C^T C (Cholesky), X0 <- X0 C^-1, Y0 <- Y0 C^-1 (eq. V0_basis)
     so that X0^T Y0 = I.  Generalized LREP: M Y0 = B X0 and X0^T B Y0 = I.
+    Parity: pinned (Example 2 closed form y0_l = l (n - l + 1) / 2).
     """
     X0 = np.asarray(X0, dtype=np.float64).reshape(op.n, -1)
     gen = getattr(op, "B", None) is not None
