@@ -149,3 +149,25 @@ def test_bosp_on_spectral_operator_vs_definition():
     out = R.bosp(op, 6, 6, 1e-10, X0=p["phi"][:, None])
     np.testing.assert_allclose(out["lam"], ref, rtol=1e-10)
     assert R.residuals(op, out["X"], out["Y"], out["lam"]).max() < 1e-10
+
+
+def test_bdg_spectral_input_conventions():
+    """The workload generator follows the example's definitions: periodic
+    grid x_j = -8 + j h on (-8, 8), h^3 sum phi_s^2 = 1, phi_s peaked at the
+    grid point x = 0 (the spectral discretisation is not sign-preserving:
+    at h = 1 its tails dip to -1e-4 of the peak), symmetric under x <-> y
+    (gamma_x = gamma_y) and under each reflection x -> -x, K phi_s = 0
+    through d_K."""
+    p = synth.bdg_spectral(16)
+    N, h = 16, 1.0
+    phi = p["phi_s"].reshape(N, N, N)  # (z, y, x)
+    assert abs(h ** 3 * float(np.sum(phi * phi)) - 1.0) < 1e-13
+    assert phi[8, 8, 8] == phi.max() and phi.min() > -1e-3 * phi.max()
+    np.testing.assert_allclose(phi, np.transpose(phi, (0, 2, 1)), atol=1e-13)
+    # x_j = -8 + j: the reflection x -> -x maps index j to (16 - j) mod 16
+    ref = np.roll(phi[:, :, ::-1], 1, axis=2)
+    np.testing.assert_allclose(phi, ref, atol=1e-13)
+    op = R.SpectralOp(N, N, N, p["lengths"], -0.5, p["dK"], p["dM"])
+    assert np.abs(op.apply("K", p["phi"])).max() < 1e-12
+    # V at the grid corner x = y = z = -8: (64 + 64 + 4 * 64) / 2
+    assert abs(p["V"][0] - 192.0) < 1e-12
