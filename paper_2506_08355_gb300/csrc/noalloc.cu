@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <string>
 
 #include "../../include/lrep_ops.h"
 #include "kernels.h"
@@ -74,6 +75,8 @@ extern "C" lrep_status lrep_op_gram_noalloc(int64_t n, int32_t a, int32_t b, con
   lrep_status s = scratch_address(&ws);
   if (s != LREP_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
+  // an error left by an earlier, unrelated call is not this call's failure
+  (void)cudaGetLastError();
   cudaError_t e;
   if (n == 0)
     e = cudaMemset2DAsync(G, ldg * sizeof(double), 0, a * sizeof(double), b, st);
@@ -81,7 +84,9 @@ extern "C" lrep_status lrep_op_gram_noalloc(int64_t n, int32_t a, int32_t b, con
     e = lrep::gram_f64_capped(n, lrep::seg1(A, lda, a), lrep::seg1(B, ldb, b), G, ldg, ws,
                               kGramScratchElems, st);
   if (e != cudaSuccess) {
-    lrep::set_global_error("lrep_op_gram_noalloc: kernel launch failed");
+    const std::string msg = std::string("lrep_op_gram_noalloc: kernel launch failed: ") +
+                            cudaGetErrorString(e);
+    lrep::set_global_error(msg.c_str());
     return LREP_ERR_CUDA;
   }
   return LREP_OK;

@@ -114,6 +114,96 @@ def haar_dense_device(n: int, seed: int, k_range=(0.5, 10.0), m_range=(0.5, 10.0
     return out
 
 
+def haar_reflectors(n: int, rng: np.random.Generator):
+    """Householder form of a Haar-random orthogonal n x n matrix, drawn
+    directly (Stewart's construction, SIAM J. Numer. Anal. 17, 1980).
+
+    Householder QR of a Gaussian matrix meets, at step j, a column whose
+    rows j..n-1 are again N(0, I) and independent of the reflectors before
+    it (orthogonal invariance), so drawing that column fresh gives the same
+    distribution.  Reflector j maps x_j ~ N(0, I_{n-j}) to beta_j e_1 in
+    LAPACK's convention (H_j = I - tau_j v_j v_j^T, v_j[0] = 1,
+    beta_j = -sign(x_j[0]) ||x_j||), and Q = H_0 H_1 ... H_{n-1} diag(sign
+    beta) is Haar (Mezzadri's sign fix of diag(R)).  Every reflector is a
+    well-conditioned function of its own draw, so two machines that form Q
+    from the same draws agree to a few units of rounding (a QR of the drawn
+    Gaussian matrix would not: its Q moves with the matrix's condition).
+
+    Returns (V, tau, sgn): V n x n Fortran-ordered with v_j in rows j.. of
+    column j (unit entry on the diagonal, zeros above), tau and sgn of
+    length n."""
+    V = np.zeros((n, n), dtype=np.float64, order="F")
+    tau = np.zeros(n)
+    sgn = np.ones(n)
+    for j in range(n):
+        x = rng.standard_normal(n - j)
+        alpha = float(x[0])
+        xnorm = float(np.sqrt(np.dot(x[1:], x[1:]))) if n - j > 1 else 0.0
+        if xnorm == 0.0:
+            beta = alpha
+            V[j, j] = 1.0
+        else:
+            beta = -math.copysign(math.hypot(alpha, xnorm), alpha)
+            tau[j] = (beta - alpha) / beta
+            V[j + 1:, j] = x[1:] * (1.0 / (alpha - beta))
+            V[j, j] = 1.0
+        sgn[j] = 1.0 if beta > 0.0 else -1.0
+    return V, tau, sgn
+
+
+def orthogonal_from_reflectors(V, tau, sgn):
+    """Q = H_0 ... H_{n-1} diag(sgn) on the host (LAPACK dorgqr, blocked);
+    V is overwritten."""
+    from scipy.linalg import lapack
+    n = V.shape[0]
+    q, _, info = lapack.dorgqr(V, tau, lwork=max(1, 64 * n), overwrite_a=1)
+    if info != 0:
+        raise RuntimeError("dorgqr info %d" % info)
+    q *= sgn[None, :]
+    return q
+
+
+def loguniform_reflected(n: int, seed: int, lo: float = 1e-2, hi: float = 1e2):
+    """Inputs of the dense mixed-precision workload: two Haar bases in
+    Householder form (``haar_reflectors``) and spectra k, m log-uniform in
+    [lo, hi], all from one seeded generator in that order.  K = Q1 diag(k)
+    Q1^T and M = Q2 diag(m) Q2^T, i.e. K = F_K F_K^T with
+    F_K = Q1 diag(sqrt k) (and F_M alike): the factors the definition route
+    takes.  Returns a dict with V1, tau1, sgn1, V2, tau2, sgn2, k, m."""
+    rng = np.random.default_rng(seed)
+    V1, t1, s1 = haar_reflectors(n, rng)
+    V2, t2, s2 = haar_reflectors(n, rng)
+    k = _draw_spectrum(rng, n, lo, hi, "loguniform")
+    m = _draw_spectrum(rng, n, lo, hi, "loguniform")
+    return {"V1": V1, "tau1": t1, "sgn1": s1, "V2": V2, "tau2": t2, "sgn2": s2,
+            "k": k, "m": m, "n": n}
+
+
+def reflected_factor_host(V, tau, sgn, spec):
+    """F = Q diag(sqrt(spec)) on the host (V is overwritten)."""
+    q = orthogonal_from_reflectors(V, tau, sgn)
+    q *= np.sqrt(spec)[None, :]
+    return q
+
+
+def reflected_operator_device(V, tau, sgn, spec, device="cuda"):
+    """A = Q diag(spec) Q^T in float64 on a CUDA device with torch (the
+    input preparation of the workload, not the solver): Q from the
+    reflectors by torch.linalg.householder_product, F = Q diag(sqrt spec),
+    A = F F^T symmetrised.  Returns a contiguous float64 device tensor."""
+    import torch
+    Vd = torch.from_numpy(V).to(device)
+    td = torch.from_numpy(np.asarray(tau)).to(device)
+    Q = torch.linalg.householder_product(Vd, td)
+    del Vd
+    scale = torch.from_numpy(np.asarray(sgn) * np.sqrt(spec)).to(device)
+    Q *= scale[None, :]
+    A = Q @ Q.T
+    del Q
+    A = 0.5 * (A + A.T)
+    return A.contiguous()
+
+
 def tridiag_T(n: int, s: float) -> np.ndarray:
     """T(s): 2 on the diagonal, -1 off it, s in the two corners (Section 4)."""
     t = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)

@@ -6,6 +6,12 @@ config1: the 64 smallest positive eigenvalues of the dense n = 8192
 workload with a 4-dimensional nullspace of K (definition route, values
 only, with the construction's factors F_K = Q1 diag(sqrt k),
 F_M = Q2 diag(sqrt m)).
+config3: the 256 smallest positive eigenvalues of the dense n = 32768
+mixed-precision workload (k, m log-uniform in [1e-2, 1e2], Haar Q1, Q2 in
+Householder form, seed 3), by the same values-only definition route from
+the factors F_K = Q1 diag(sqrt k), F_M = Q2 diag(sqrt m).  About 1.5 h on
+8 cores and ~40 GB of host memory (two dorgqr, one GEMM and one
+values-only SVD of order 32768).
 """
 import os
 import sys
@@ -32,6 +38,29 @@ def config1():
                 "# (synth.config(1): Haar Q1, Q2 seed 1, k, m ~ U[0.5, 10], 4 zero k),\n"
                 "# definition route of the oracle (values-only SVD); written by\n"
                 "# tests/golden/make_golden.py config1\n")
+        for v in lam:
+            f.write("%.17e\n" % v)
+    print(path)
+
+
+def config3():
+    import time
+    t0 = time.perf_counter()
+    g = synth.loguniform_reflected(32768, seed=3)
+    FK = synth.reflected_factor_host(g["V1"], g["tau1"], g["sgn1"], g["k"])
+    del g["V1"]
+    FM = synth.reflected_factor_host(g["V2"], g["tau2"], g["sgn2"], g["m"])
+    del g["V2"]
+    t1 = time.perf_counter()
+    lam = R.lrep_definition_values(FK, FM, 256)
+    dt = time.perf_counter() - t0
+    path = os.path.join(HERE, "config3_lambda.txt")
+    with open(path, "w") as f:
+        f.write("# 256 smallest positive eigenvalues of the dense n = 32768 workload\n"
+                "# (synth.loguniform_reflected(32768, seed=3): Haar Q1, Q2 in Householder\n"
+                "# form, k, m log-uniform in [1e-2, 1e2]), definition route of the oracle\n"
+                "# (values-only SVD of F_K^T F_M); factors %.0f s, total %.0f s; written by\n"
+                "# tests/golden/make_golden.py config3\n" % (t1 - t0, dt))
         for v in lam:
             f.write("%.17e\n" % v)
     print(path)
