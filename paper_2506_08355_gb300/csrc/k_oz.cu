@@ -259,11 +259,11 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ C
   __syncthreads();
   if (threadIdx.x == 0) {
     // every MMA this CTA issued has completed; no TMA copy is left in flight
-    mbar_wait(smem_u32(done), 0, err, 17);
+    mbar_drain(smem_u32(done), 0, err, 17);
     for (int q = cnt[2]; q < cnt[0]; ++q)
-      if (!mbar_wait(smem_u32(&fullA[q % G::NSA]), (q / G::NSA) & 1, err, 18)) break;
+      if (!mbar_drain(smem_u32(&fullA[q % G::NSA]), (q / G::NSA) & 1, err, 18)) break;
     for (int j = cnt[3]; j < cnt[1]; ++j)
-      if (!mbar_wait(smem_u32(&fullB[j & 1]), (j >> 1) & 1, err, 19)) break;
+      if (!mbar_drain(smem_u32(&fullB[j & 1]), (j >> 1) & 1, err, 19)) break;
   }
   fence_before();
   __syncthreads();

@@ -127,7 +127,7 @@ bf16x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ 
     __syncwarp();
   }
   // epilogue: TMEM lane = output row; warp w owns lanes 32w..32w+31
-  const bool ok = mbar_wait(smem_u32(done), 0, err, 3);
+  const bool ok = mbar_drain(smem_u32(done), 0, err, 3);
   asm volatile("tcgen05.fence::after_thread_sync;");
   const int row = tile_m * BM + warp * 32 + lane;
   if (ok) {
@@ -155,13 +155,275 @@ bf16x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ 
   // drain TMA copies that were issued but not consumed (error path only)
   if (threadIdx.x == 0) {
     for (int it = counts[1]; it < counts[0]; ++it)
-      if (!mbar_wait(smem_u32(&full[it % STAGES]), (it / STAGES) & 1, err, 4)) break;
+      if (!mbar_drain(smem_u32(&full[it % STAGES]), (it / STAGES) & 1, err, 4)) break;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(tmem_cols));
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric form: A = A^T, so only the tiles A_IJ with I <= J (128 x 128) are
+// read, and each off-diagonal tile serves both Y_I += A_IJ X_J and
+// Y_J += A_IJ^T X_I (the second MMA reads the same shared-memory tile as an
+// MN-major operand: no transposed copy).  HBM traffic is about half the
+// matrix.  Work items are super-blocks of b x b tiles (super-rows S <= C):
+// an off-diagonal item keeps 2b fp32 accumulators in tensor memory (b for
+// its rows I, b for its columns J), a diagonal item b.  Each item writes its
+// accumulators once to a slot of the partial buffer (slot (S, C) for the
+// rows of S, slot (C, S) for the rows of C; (S, S) for a diagonal item), so
+// every super-row has exactly Tsb slots, summed in fixed order in float64.
+// Persistent CTAs take items round-robin (off-diagonal ones first); one
+// thread issues TMA (2 stages of one tile each), one issues MMA, four warps
+// drain the accumulators.
+constexpr int SYM_STAGES = 2;
+constexpr int SYM_TILE = 128;
+constexpr int SYM_BOX = BM * BK * 2;  // one 128 x 64 bf16 box: 16 KB
+
+__device__ __forceinline__ void sym_item(int q, int Tsb, int& S, int& C) {
+  const int noff = Tsb * (Tsb - 1) / 2;
+  if (q >= noff) {
+    S = C = q - noff;
+    return;
+  }
+  int s = 0, rem = q;
+  while (rem >= Tsb - 1 - s) {
+    rem -= Tsb - 1 - s;
+    ++s;
+  }
+  S = s;
+  C = s + 1 + rem;
+}
+
+// tiles of item (S, C) in issue order; returns false past the last one
+__device__ __forceinline__ bool sym_next(int S, int C, int b, int T, int& i, int& j) {
+  const bool diag = (S == C);
+  for (;;) {
+    ++j;
+    if (j >= b) {
+      ++i;
+      if (i >= b) return false;
+      j = diag ? i : 0;
+    }
+    if (S * b + i < T && C * b + j < T) return true;
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(192, 1)
+bf16x3_sym_kernel(const __grid_constant__ CUtensorMap mAhi,
+                  const __grid_constant__ CUtensorMap mAlo,
+                  const __grid_constant__ CUtensorMap mXhi,
+                  const __grid_constant__ CUtensorMap mXlo, int n, int c, int b, int T,
+                  int Tsb, int items, int tmem_cols, float* __restrict__ part,
+                  int* __restrict__ err, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int XBOX = N * BK * 2;                  // one N x 64 bf16 box
+  constexpr int STAGE = 4 * SYM_BOX + 8 * XBOX;     // A hi/lo + X_J, X_I hi/lo
+  uint64_t* bars = (uint64_t*)(base + SYM_STAGES * STAGE);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + SYM_STAGES;
+  uint64_t* accf = bars + 2 * SYM_STAGES;       // accumulators of an item complete
+  uint64_t* acce = bars + 2 * SYM_STAGES + 1;   // accumulators drained
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * SYM_STAGES + 2);
+  // [0] stages issued [1] stages consumed [2] items committed to accf
+  volatile int* counts = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SYM_STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(accf), 1);
+    mbar_init(smem_u32(acce), 4);
+    counts[0] = 0;
+    counts[1] = 0;
+    counts[2] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32((const void*)tmem_slot), tmem_cols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int rows_sr = b * SYM_TILE;  // rows of one super-row
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer: every tile of this CTA's items in order
+      int it = 0;
+      bool stop = false;
+      for (int q = blockIdx.x; q < items && !stop; q += gridDim.x) {
+        int S, C;
+        sym_item(q, Tsb, S, C);
+        int i = 0, j = -1;
+        while (sym_next(S, C, b, T, i, j)) {
+          const int sidx = it % SYM_STAGES;
+          if (it >= SYM_STAGES &&
+              !mbar_wait(smem_u32(&empty[sidx]), ((it / SYM_STAGES) - 1) & 1, err, 21)) {
+            stop = true;
+            break;
+          }
+          if (*(volatile int*)err) {
+            stop = true;
+            break;
+          }
+          uint8_t* st = base + sidx * STAGE;
+          const uint32_t fb = smem_u32(&full[sidx]);
+          mbar_expect_tx(fb, (uint32_t)STAGE);
+          const int I = (S * b + i) * SYM_TILE, J = (C * b + j) * SYM_TILE;
+          tma_load_2d(smem_u32(st), &mAhi, fb, J, I);
+          tma_load_2d(smem_u32(st + SYM_BOX), &mAhi, fb, J + BK, I);
+          tma_load_2d(smem_u32(st + 2 * SYM_BOX), &mAlo, fb, J, I);
+          tma_load_2d(smem_u32(st + 3 * SYM_BOX), &mAlo, fb, J + BK, I);
+          uint8_t* xs = st + 4 * SYM_BOX;
+          tma_load_2d(smem_u32(xs), &mXhi, fb, J, 0);
+          tma_load_2d(smem_u32(xs + XBOX), &mXhi, fb, J + BK, 0);
+          tma_load_2d(smem_u32(xs + 2 * XBOX), &mXlo, fb, J, 0);
+          tma_load_2d(smem_u32(xs + 3 * XBOX), &mXlo, fb, J + BK, 0);
+          tma_load_2d(smem_u32(xs + 4 * XBOX), &mXhi, fb, I, 0);
+          tma_load_2d(smem_u32(xs + 5 * XBOX), &mXhi, fb, I + BK, 0);
+          tma_load_2d(smem_u32(xs + 6 * XBOX), &mXlo, fb, I, 0);
+          tma_load_2d(smem_u32(xs + 7 * XBOX), &mXlo, fb, I + BK, 0);
+          ++it;
+        }
+      }
+      counts[0] = it;
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idd = idesc_bf16(BM, N);               // A_IJ X_J
+      constexpr uint32_t idt = idesc_bf16(BM, N) | (1u << 15);  // A_IJ^T X_I (A MN-major)
+      int it = 0, nitem = 0;
+      bool stop = false;
+      for (int q = blockIdx.x; q < items && !stop; q += gridDim.x, ++nitem) {
+        int S, C;
+        sym_item(q, Tsb, S, C);
+        const bool diag = (S == C);
+        // the previous item's accumulators must be drained first
+        if (nitem > 0 && !mbar_wait(smem_u32(acce), (nitem - 1) & 1, err, 22)) break;
+        fence_after();
+        uint32_t fresh = 0xFFFFFFFFu;  // accumulators not yet written in this item
+        int i = 0, j = -1;
+        while (sym_next(S, C, b, T, i, j)) {
+          const int sidx = it % SYM_STAGES;
+          if (!mbar_wait(smem_u32(&full[sidx]), (it / SYM_STAGES) & 1, err, 23)) {
+            stop = true;
+            break;
+          }
+          fence_after();
+          uint8_t* st = base + sidx * STAGE;
+          const uint32_t ahi = smem_u32(st), alo = smem_u32(st + 2 * SYM_BOX);
+          const uint32_t xs = smem_u32(st + 4 * SYM_BOX);
+          const uint32_t xjh = xs, xjl = xs + 2 * XBOX, xih = xs + 4 * XBOX,
+                         xil = xs + 6 * XBOX;
+          // direct: rows I, contraction over J (two 64-wide boxes)
+          {
+            const int a = i;
+            const uint32_t d = tmem + (uint32_t)(a * N);
+            uint32_t acc = (fresh >> a) & 1u ? 0u : 1u;
+            fresh &= ~(1u << a);
+#pragma unroll
+            for (int kk = 0; kk < SYM_TILE / 16; ++kk) {
+              const uint32_t bo = (uint32_t)((kk >> 2) * SYM_BOX + (kk & 3) * 32);
+              const uint32_t xo = (uint32_t)((kk >> 2) * XBOX + (kk & 3) * 32);
+              mma_bf16(d, sdesc(ahi + bo), sdesc(xjh + xo), idd, acc);
+              mma_bf16(d, sdesc(ahi + bo), sdesc(xjl + xo), idd, 1u);
+              mma_bf16(d, sdesc(alo + bo), sdesc(xjh + xo), idd, 1u);
+              acc = 1u;
+            }
+          }
+          // transposed: rows J, contraction over I (16 tile rows per step)
+          if (!(diag && i == j)) {
+            const int a = diag ? j : b + j;
+            const uint32_t d = tmem + (uint32_t)(a * N);
+            uint32_t acc = (fresh >> a) & 1u ? 0u : 1u;
+            fresh &= ~(1u << a);
+#pragma unroll
+            for (int kk = 0; kk < SYM_TILE / 16; ++kk) {
+              const uint32_t ro = (uint32_t)(kk * 16 * 128);
+              const uint32_t xo = (uint32_t)((kk >> 2) * XBOX + (kk & 3) * 32);
+              mma_bf16(d, sdesc_mn(ahi + ro, SYM_BOX), sdesc(xih + xo), idt, acc);
+              mma_bf16(d, sdesc_mn(ahi + ro, SYM_BOX), sdesc(xil + xo), idt, 1u);
+              mma_bf16(d, sdesc_mn(alo + ro, SYM_BOX), sdesc(xih + xo), idt, 1u);
+              acc = 1u;
+            }
+          }
+          mma_commit(smem_u32(&empty[sidx]));
+          ++it;
+        }
+        mma_commit(smem_u32(accf));
+        counts[2] = nitem + 1;
+      }
+      counts[1] = it;
+    }
+    __syncwarp();
+  } else {  // warps 2..5: drain one item's accumulators into its partial slots
+    const int q4 = warp & 3;
+    const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
+    int nitem = 0;
+    for (int q = blockIdx.x; q < items; q += gridDim.x, ++nitem) {
+      int S, C;
+      sym_item(q, Tsb, S, C);
+      const bool diag = (S == C);
+      if (!mbar_wait(smem_u32(accf), nitem & 1, err, 24)) break;
+      fence_after();
+      const int nacc = diag ? b : 2 * b;
+      for (int a = 0; a < nacc; ++a) {
+        const int sr = (a < b) ? S : C;   // super-row of these rows
+        const int tt = (a < b) ? C : S;   // slot within the super-row
+        const int blk = (a < b) ? a : a - b;
+        if (sr * b + blk >= T) continue;  // rows past the matrix: never written
+        const int rl = blk * SYM_TILE + q4 * 32 + lane;
+        float* dst = part + ((int64_t)(sr * Tsb + tt) * c) * rows_sr + rl;
+#pragma unroll
+        for (int j0 = 0; j0 < N; j0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(tmem + lanes + (uint32_t)(a * N + j0), v);
+          tmem_ld_wait();
+#pragma unroll
+          for (int qq = 0; qq < 16; ++qq)
+            if (j0 + qq < c) dst[(int64_t)(j0 + qq) * rows_sr] = __uint_as_float(v[qq]);
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(acce));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // this CTA's MMAs and TMA copies have landed before tensor memory is freed
+    const int committed = counts[2];
+    if (committed > 0) mbar_drain(smem_u32(accf), (committed - 1) & 1, err, 25);
+    for (int it = counts[1]; it < counts[0]; ++it)
+      if (!mbar_drain(smem_u32(&full[it % SYM_STAGES]), (it / SYM_STAGES) & 1, err, 26)) break;
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, tmem_cols);
+}
+
+// Y (float64) = sum over the Tsb slots of each super-row, in slot order
+__global__ void sym_reduce_kernel(int64_t n, int c, int rows_sr, int Tsb,
+                                  const float* __restrict__ part, double* __restrict__ Y,
+                                  int64_t ldy, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t tot = n * c;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n, r = e % n;
+    const int64_t sr = r / rows_sr, rl = r % rows_sr;
+    const float* src = part + ((sr * Tsb) * c + j) * rows_sr + rl;
+    double s = 0.0;
+    for (int t = 0; t < Tsb; ++t) s += (double)src[(int64_t)t * c * rows_sr];
+    Y[r + j * ldy] = s;
+  }
 }
 
 __global__ void split_bf16_kernel(int64_t rows, int64_t cols, const double* __restrict__ A,
@@ -262,9 +524,46 @@ bool tc_make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t oute
   return r == CUDA_SUCCESS;
 }
 
+namespace {
+
+// super-block edge b (tiles) of the symmetric kernel: the largest with 2 b N
+// tensor-memory columns that still gives about two waves of items on the
+// 152 SMs (b = 1 when even that is impossible)
+struct SymPlan {
+  int b, T, Tsb, items;
+};
+SymPlan sym_plan(int64_t n, int N) {
+  SymPlan p{};
+  p.T = (int)((n + SYM_TILE - 1) / SYM_TILE);
+  p.b = 1;
+  for (int b = 256 / N; b >= 1; --b) {
+    const int tsb = (p.T + b - 1) / b;
+    if ((int64_t)tsb * (tsb + 1) / 2 >= 2 * kNumSMs) {
+      p.b = b;
+      break;
+    }
+  }
+  p.Tsb = (p.T + p.b - 1) / p.b;
+  p.items = p.Tsb * (p.Tsb + 1) / 2;
+  return p;
+}
+
+bool use_sym(int c) { return c <= 32; }
+
+size_t sym_part_bytes(int64_t n, int c) {
+  const int N = c <= 16 ? 16 : 32;
+  const SymPlan p = sym_plan(n, N);
+  return (size_t)p.Tsb * p.Tsb * c * (size_t)(p.b * SYM_TILE) * 4;
+}
+
+}  // namespace
+
+// monotone in c: room for any product of up to c columns
 size_t tc_ws_bytes(int64_t n, int c) {
   const int64_t ldb = tc_ld(n);
-  return (size_t)2 * ldb * c * 2 + (size_t)tc_splits(n) * c * n * 4 + 4096;
+  size_t part = sym_part_bytes(n, std::min(c, 32));
+  if (!use_sym(c)) part = std::max(part, (size_t)tc_splits(n) * c * n * 4);
+  return (size_t)2 * ldb * c * 2 + part + 4096;
 }
 
 cudaError_t tc_apply(const TcOperand& A, int64_t n, int c, const double* X, int64_t ldx,
@@ -284,6 +583,39 @@ cudaError_t tc_apply(const TcOperand& A, int64_t n, int c, const double* X, int6
   CUtensorMap mxh, mxl;
   if (!tc_make_map(&mxh, xhi, n, c, ldb, BK, N) || !tc_make_map(&mxl, xlo, n, c, ldb, BK, N))
     return cudaErrorInvalidValue;
+  if (use_sym(c)) {
+    const SymPlan pl = sym_plan(n, N);
+    const int nacc = (pl.Tsb > 1 ? 2 : 1) * pl.b;
+    int tcols = 32;
+    while (tcols < nacc * N) tcols <<= 1;
+    const int stage = 4 * SYM_BOX + 8 * N * BK * 2;
+    const size_t smem = (size_t)SYM_STAGES * stage + 1024 + 256;
+    const int grid = std::min(pl.items, kNumSMs);
+    const int rows_sr = pl.b * SYM_TILE;
+    if (N == 16) {
+      static const cudaError_t a16 = cudaFuncSetAttribute(
+          bf16x3_sym_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      if (a16 != cudaSuccess) return a16;
+      bf16x3_sym_kernel<16><<<grid, 192, smem, st>>>(A.hi_map, A.lo_map, mxh, mxl, (int)n, c,
+                                                     pl.b, pl.T, pl.Tsb, pl.items, tcols, part,
+                                                     err, skip); LREP_COUNT_LAUNCH();
+    } else {
+      static const cudaError_t a32 = cudaFuncSetAttribute(
+          bf16x3_sym_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      if (a32 != cudaSuccess) return a32;
+      bf16x3_sym_kernel<32><<<grid, 192, smem, st>>>(A.hi_map, A.lo_map, mxh, mxl, (int)n, c,
+                                                     pl.b, pl.T, pl.Tsb, pl.items, tcols, part,
+                                                     err, skip); LREP_COUNT_LAUNCH();
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t tot = n * c;
+    const unsigned g =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 8 * kNumSMs));
+    sym_reduce_kernel<<<g, 256, 0, st>>>(n, c, rows_sr, pl.Tsb, part, Y, ldy, skip);
+    LREP_COUNT_LAUNCH();
+    return cudaGetLastError();
+  }
   const int kt = (int)((n + BK - 1) / BK);
   const int per = tc_per(n);
   const int s = (kt + per - 1) / per;

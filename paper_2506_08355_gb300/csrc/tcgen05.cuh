@@ -36,9 +36,24 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait; returns false (and records `code`) when the limit expires
-// or when another thread of the grid already recorded an error
+// bounded wait for the pipeline: returns false (and records `code`) when the
+// limit expires, or when another CTA already recorded an error (the flag is
+// polled every 256 tries, so the grid gives up soon after the first CTA does)
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err, int code) {
+  const long long t0 = clock64();
+  unsigned tries = 0;
+  while (!mbar_try(a, parity)) {
+    if ((++tries & 255u) == 0 && *(volatile int*)err != 0) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicExch(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+// bounded wait that ignores other CTAs' errors: for this CTA's own copies and
+// MMAs in flight, which must land before it frees tensor memory and exits
+__device__ __forceinline__ bool mbar_drain(uint32_t a, uint32_t parity, int* err, int code) {
   const long long t0 = clock64();
   while (!mbar_try(a, parity)) {
     if (clock64() - t0 > WAIT_CYCLES) {
@@ -67,6 +82,20 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   d |= (uint64_t)(1024 >> 4) << 32;     // SBO
   d |= (uint64_t)1 << 46;               // version
   d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+  return d;
+}
+
+// shared-memory matrix descriptor of an MN-major operand with 128-byte
+// swizzle: the tile holds K rows of 128 bytes (64 consecutive M/N values
+// each), 8-row swizzle atoms 1024 bytes apart along K (SBO) and 64-value
+// atoms `lbo` bytes apart along M/N (LBO), descriptor version 1
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;  // LBO: stride between M/N atoms
+  d |= (uint64_t)(1024 >> 4) << 32;             // SBO: stride between 8-row K groups
+  d |= (uint64_t)1 << 46;                       // version
+  d |= (uint64_t)2 << 61;                       // SWIZZLE_128B
   return d;
 }
 

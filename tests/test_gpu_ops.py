@@ -221,16 +221,23 @@ def test_philox_normals(L):
     np.testing.assert_allclose(from_dev(out), ref, rtol=1e-13, atol=1e-14)
 
 
-@pytest.mark.parametrize("n,c", [(1000, 16), (1000, 1), (777, 37), (4096, 32)])
+@pytest.mark.parametrize("n,c", [(1000, 16), (1000, 1), (777, 37), (4096, 32), (200, 4),
+                                 (8192, 16), (12000, 32), (12000, 17), (5000, 64)])
 def test_bf16x3_tensor_core_product(L, n, c):
     """Mixed-precision CG product (tcgen05, bf16 hi/lo split, fp32
     accumulation) against the float64 product.  Error model: dropping the
     lo*lo term and rounding lo leave ~2^-16 relative per operand, fp32
-    accumulation adds ~k 2^-24; bound 1e-4 of |A||X| with margin."""
+    accumulation adds ~k 2^-24; bound 1e-4 of |A||X| with margin.
+    Up to 32 columns the symmetric kernel runs (upper tiles only, each
+    off-diagonal tile used as A_IJ and A_IJ^T): n = 200 and 1000 have one
+    tile per super-block, n = 8192 (c = 16) super-blocks of 2 x 2 tiles and
+    n = 12000 of 3 x 3 tiles with a ragged last super-row and tile; c = 37
+    and 64 take the split-K kernel."""
     rng = np.random.default_rng(n + c)
     A = rng.standard_normal((n, n))
     K = (A + A.T) * 0.5
-    M = K @ K / n + np.eye(n)
+    del A
+    M = (K @ K / n + np.eye(n)) if n <= 4096 else (0.3 * K + 2.0 * np.eye(n))
     X = rng.standard_normal((n, c))
     p = L.Problem.dense(K, M)
     p.set_options(precision=L.PREC_MIXED_BF16X3)
