@@ -231,6 +231,28 @@ lrep_status lrep_set_start(lrep_problem p, int32_t ncols, const double* U0,
  * error. */
 lrep_status lrep_solve(lrep_problem p, int32_t nev, int32_t block, double tol);
 
+/* The same solve in steps, batch by batch (Section 3.3: with the moving
+ * window the eigenpairs are computed batch by batch, 2*nb of them locked
+ * at a time).  lrep_solve_begin runs Steps 1-2 (random start, projection
+ * off V0, Alg. 1) and returns; lrep_solve_advance then runs outer
+ * iterations of Alg. 2 until `locks` (>= 1) more lock events have happened
+ * (each locks the converged 2*nb-pair prefix of the window, or the
+ * remaining nev - locked pairs) or the solve ends, always stopping between
+ * iterations.  *locked (may be NULL) receives the number of pairs locked so
+ * far in this solve.  *done (may be NULL) is set to 1 when the solve has ended:
+ * the return value is then the solve's status (LREP_OK, LREP_NOT_CONVERGED
+ * or an error) and the results are queryable exactly as after lrep_solve;
+ * before that it returns LREP_OK and lrep_query reports LREP_ERR_STATE
+ * (except for the LREP_Q_PROFILE* queries, which report the work so far).
+ * lrep_solve_begin(p, ...) followed by lrep_solve_advance until done gives
+ * the same iterations and results as lrep_solve(p, ...).  Any other call
+ * that changes the problem (options, nullspace, start, mass matrix,
+ * lrep_solve, lrep_destroy) ends a solve in progress; LREP_ERR_STATE when
+ * advancing without one. */
+lrep_status lrep_solve_begin(lrep_problem p, int32_t nev, int32_t block, double tol);
+lrep_status lrep_solve_advance(lrep_problem p, int32_t locks, int32_t* locked,
+                               int32_t* done);
+
 /* What lrep_query returns.  dst receives dst_bytes at most; mem is
  * LREP_MEM_HOST or LREP_MEM_DEVICE_COPY (device destination). */
 enum {
@@ -253,8 +275,25 @@ enum {
                             product flops (2 nnz per column), and product
                             algorithmic bytes (operator read once per
                             launch + input and output blocks)             */
-  LREP_Q_PROFILE_CG = 14 /* float64[4]: the same for the products of the CG
+  LREP_Q_PROFILE_CG = 14,/* float64[4]: the same for the products of the CG
                             operator alone (eq. block_GS)                 */
+  LREP_Q_PROFILE_CLASSES = 15 /* float64[2 * LREP_PC_COUNT] with
+                            options.profile set: (device seconds, timed
+                            spans) of each LREP_PC_* class of solver work,
+                            every span timed by CUDA events on the
+                            problem's stream                              */
+};
+/* Classes of solver work in LREP_Q_PROFILE_CLASSES. */
+enum {
+  LREP_PC_PROD_CG = 0, /* CG operator products (eq. block_GS)              */
+  LREP_PC_PROD = 1,    /* float64-accurate operator products               */
+  LREP_PC_GRAM = 2,    /* tall-skinny Grams (eq. hat_H, projections, Alg. 1) */
+  LREP_PC_UPDATE = 3,  /* block updates (pullback, P~, projections, Alg. 1)  */
+  LREP_PC_SMALL = 4,   /* small LREP and eq. hat_pq                        */
+  LREP_PC_CGVEC = 5,   /* CG vector updates (alpha, x/r update, directions) */
+  LREP_PC_ALG1 = 6,    /* Alg. 1 coefficients on the Gram                  */
+  LREP_PC_OTHER = 7,   /* residuals, right-hand sides, column norms        */
+  LREP_PC_COUNT = 8
 };
 lrep_status lrep_query(lrep_problem p, int32_t what, void* dst,
                        int64_t dst_bytes, int32_t mem);

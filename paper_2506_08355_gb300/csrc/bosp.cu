@@ -189,9 +189,10 @@ struct Solver {
   SmallBatcher* batcher = nullptr;
   struct Pending {
     cudaEvent_t a, b;
-    int c;
+    int c;     // product columns, or -1 for a span that is not a product
     bool cgop;
     int flag;  // index into h->pflag, or -1 (product always runs)
+    int cls;   // LREP_PC_* class of the span
   };
   std::vector<cudaEvent_t> prof_free, prof_all;
   std::vector<Pending> prof_pending;
@@ -213,7 +214,11 @@ struct Solver {
     for (const Pending& q : prof_pending) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, q.a, q.b);
-      if (q.flag < 0 || h->pflag[q.flag] == 0) account_product(q.c, ms, q.cgop);
+      if (q.flag < 0 || h->pflag[q.flag] == 0) {
+        if (q.c >= 0) account_product(q.c, ms, q.cgop);
+        p->prof_class[2 * q.cls] += ms * 1e-3;
+        p->prof_class[2 * q.cls + 1] += 1.0;
+      }
       prof_free.push_back(q.a);
       prof_free.push_back(q.b);
     }
@@ -236,6 +241,23 @@ struct Solver {
   lrep_status sync() {
     LCK(cudaStreamSynchronize(st));
     if (!prof_pending.empty()) resolve_profile();
+    return LREP_OK;
+  }
+
+  // With options.profile set, f's device work is timed by CUDA events on
+  // the solver's stream and accounted to class cls (LREP_Q_PROFILE_CLASSES).
+  template <class F>
+  lrep_status timed(int cls, F&& f) {
+    if (!p->opts.profile) return f();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LST(take_event(&e0));
+    LST(take_event(&e1));
+    LCK(cudaEventRecord(e0, st));
+    const lrep_status s = f();
+    if (s != LREP_OK) return s;
+    LCK(cudaEventRecord(e1, st));
+    prof_pending.push_back(Pending{e0, e1, -1, false, -1, cls});
+    if (prof_pending.size() >= 512) LST(sync());
     return LREP_OK;
   }
 
@@ -378,6 +400,9 @@ struct Solver {
     return t_sl < 0.5 * t_fp;
   }
   lrep_status gram(const Segs& A, const Segs& B, double* G, int64_t ldg) {
+    return timed(LREP_PC_GRAM, [&] { return gram_(A, B, G, ldg); });
+  }
+  lrep_status gram_(const Segs& A, const Segs& B, double* G, int64_t ldg) {
     if (oz && 2.0 * n * A.total() * B.total() >= kSlicedMinFlops &&
         sliced_gram_pays(A.total(), B.total())) {
       LCK(oz_gram(n, A, B, G, ldg, ozws, ozws_bytes, p->op.tc_err, st));
@@ -390,6 +415,10 @@ struct Solver {
   }
   lrep_status update(int c, double alpha, const Segs& A, const double* B,
                      int64_t ldb, double beta, double* Cm) {
+    return timed(LREP_PC_UPDATE, [&] { return update_(c, alpha, A, B, ldb, beta, Cm); });
+  }
+  lrep_status update_(int c, double alpha, const Segs& A, const double* B,
+                      int64_t ldb, double beta, double* Cm) {
     if (oz && beta != 0.0 && 2.0 * n * A.total() * c >= kSlicedMinFlops &&
         sliced_update_pays(A.total(), c)) {
       LCK(oz_update(n, A.total(), c, alpha, A, B, ldb, beta, Cm, ld, ozws, ozws_bytes,
@@ -419,7 +448,7 @@ struct Solver {
         flag = (int)prof_pending.size();
         LCK(cudaMemcpyAsync(&h->pflag[flag], skip, sizeof(int), cudaMemcpyDeviceToHost, st));
       }
-      prof_pending.push_back(Pending{e0, e1, c, cgop, flag});
+      prof_pending.push_back(Pending{e0, e1, c, cgop, flag, cgop ? LREP_PC_PROD_CG : LREP_PC_PROD});
       if (prof_pending.size() >= 512) LST(sync());
     }
     return s;
@@ -433,7 +462,9 @@ struct Solver {
       nnz = (double)n * n;
       const int prec = p->opts.precision;
       if (cgop && (prec & LREP_PREC_MIXED_BF16X3))
-        opbytes = 4.0 * nnz;   // hi + lo bf16
+        // hi + lo bf16; up to 32 columns the symmetric kernel needs only the
+        // tiles on and above the diagonal
+        opbytes = (c <= 32 ? 2.0 : 4.0) * nnz;
       else if (prec & LREP_PREC_FP64_SLICED)
         opbytes = 14.0 * nnz;  // 7 bf16 digit planes
       else
@@ -466,12 +497,18 @@ struct Solver {
   lrep_status cg_solve(int which, int c, const double* B, double* X, double ctol,
                        int maxit, int check_every, bool cgop) {
     LCK(cudaMemsetAsync(cg.iters, 0, sizeof(int), st));
-    LCK(cg_init(n, c, B, ld, X, Rr, Pr, ld, ctol, cg, st));
+    LST(timed(LREP_PC_CGVEC, [&] {
+      LCK(cg_init(n, c, B, ld, X, Rr, Pr, ld, ctol, cg, st));
+      return LREP_OK;
+    }));
     for (int it = 0; it < maxit; ++it) {
       LST(apply(which, c, Pr, Qr, cg.done, cgop));
-      LCK(cg_alpha(n, c, Pr, Qr, ld, cg, st));
-      LCK(cg_update(n, c, X, Rr, Pr, Qr, ld, cg, st));
-      LCK(cg_pdir(n, c, Rr, Pr, ld, cg, st));
+      LST(timed(LREP_PC_CGVEC, [&] {
+        LCK(cg_alpha(n, c, Pr, Qr, ld, cg, st));
+        LCK(cg_update(n, c, X, Rr, Pr, Qr, ld, cg, st));
+        LCK(cg_pdir(n, c, Rr, Pr, ld, cg, st));
+        return LREP_OK;
+      }));
       if (check_every > 0 && (it + 1) % check_every == 0) {
         int done = 0;
         LCK(cudaMemcpyAsync(&h->cnt[3], cg.done, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -508,8 +545,11 @@ struct Solver {
     Segs s = seg_push(seg1(Ain, ld, m), Bin, ld, m);
     Segs sb = bc ? seg_push(seg1(BAin, ld, m), BBin, ld, m) : s;
     LST(gram(s, sb, G2, ldg));
-    LCK(biorth_coef(m, G2, ldg, refa2, refb2, tau, cA, cB, dmax, cwork, cnt_d, st,
-                    near_identity));
+    LST(timed(LREP_PC_ALG1, [&] {
+      LCK(biorth_coef(m, G2, ldg, refa2, refb2, tau, cA, cB, dmax, cwork, cnt_d, st,
+                      near_identity));
+      return LREP_OK;
+    }));
     LCK(cudaMemcpyAsync(&h->cnt[0], cnt_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     LST(sync());
     const int k1 = h->cnt[0];
@@ -527,8 +567,11 @@ struct Solver {
     Segs s2 = seg_push(seg1(tA, ld, k1), tB, ld, k1);
     Segs s2b = bc ? seg_push(seg1(tBA, ld, k1), tBB, ld, k1) : s2;
     LST(gram(s2, s2b, G2, ldg));
-    LCK(biorth_coef(k1, G2, ldg, nullptr, nullptr, tau, cA2, cB2, dmax, cwork, cnt_d, st,
-                    true));
+    LST(timed(LREP_PC_ALG1, [&] {
+      LCK(biorth_coef(k1, G2, ldg, nullptr, nullptr, tau, cA2, cB2, dmax, cwork, cnt_d, st,
+                      true));
+      return LREP_OK;
+    }));
     LCK(cudaMemcpyAsync(&h->cnt[0], cnt_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     LST(sync());
     const int k2 = h->cnt[0];
@@ -644,10 +687,13 @@ struct Solver {
     job.lam = lam_d; job.Xh = Xh; job.Yh = Yh; job.ldo = dmax;
     job.work = swork; job.info = info_d; job.biorth_err = berr_d;
     job.d = d; job.w_prev = w_prev;
-    if (batcher)
-      LCK(batcher->run(job, st));
-    else
-      LCK(small_lrep_one(job, st));
+    LST(timed(LREP_PC_SMALL, [&] {
+      if (batcher)
+        LCK(batcher->run(job, st));
+      else
+        LCK(small_lrep_one(job, st));
+      return LREP_OK;
+    }));
     const int t = nx();
     LST(update(e, 0.0, sU, Xh, dmax, 1.0, UX[t]));
     LST(update(e, 0.0, sV, Yh, dmax, 1.0, UY[t]));
@@ -658,8 +704,11 @@ struct Solver {
       LST(update(e, 0.0, seg1(BVcur(), ld, d), Yh, dmax, 1.0, BV[t]));
     }
     if (events) LCK(cudaEventRecord(ev[1], st));
-    LCK(residuals_f64(n, e, UX[t], UY[t], KX[t], MY[t], ld, lam_d, eps_d, part,
-                      counters, st, gen ? BU[t] : nullptr, gen ? BV[t] : nullptr));
+    LST(timed(LREP_PC_OTHER, [&] {
+      LCK(residuals_f64(n, e, UX[t], UY[t], KX[t], MY[t], ld, lam_d, eps_d, part,
+                        counters, st, gen ? BU[t] : nullptr, gen ? BV[t] : nullptr));
+      return LREP_OK;
+    }));
     LCK(cudaMemcpyAsync(h->lam, lam_d, sizeof(double) * d, cudaMemcpyDeviceToHost, st));
     LCK(cudaMemcpyAsync(h->eps, eps_d, sizeof(double) * e, cudaMemcpyDeviceToHost, st));
     LCK(cudaMemcpyAsync(&h->berr, berr_d, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -734,16 +783,33 @@ struct Solver {
   }
 
   // ------------------------------------------------------------- solve
-  lrep_status run() {
+  // outer-iteration state kept between calls of iterate()
+  int it_ = 0;
+  bool converged_ = false;
+
+  lrep_status begin() {
     auto t0 = std::chrono::steady_clock::now();
     LST(setup());
     LST(sync());
     p->timings[0] += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    it_ = 0;
+    converged_ = false;
+    return LREP_OK;
+  }
+
+  // Outer iterations of Alg. 2 until `max_locks` lock events (Section 3.3:
+  // each locks 2 nb converged pairs, or the last nev - locked) have happened
+  // in this call, or the solve has ended (*ended = true: converged or maxit;
+  // the results are then final and the return value is the solve's status).
+  // Stops only at iteration boundaries, so the next call continues exactly
+  // where this one left off.
+  lrep_status iterate(int max_locks, bool* ended) {
+    *ended = false;
     const int maxit = p->opts.maxit;
     const int every = std::max(1, p->opts.refresh_every);
-    bool converged = false;
-    int it = 0;
-    for (it = 1; it <= maxit; ++it) {
+    int locks = 0;
+    while (it_ < maxit) {
+      const int it = ++it_;
       if (it > 1 && it % every == 0) LST(refresh());
       const int want_max = std::min(w, d);
       int e = std::min(d, want_max + (moving ? 2 * nb : 0));
@@ -781,12 +847,13 @@ struct Solver {
                 it, d, ell, c, want, emax, h->lam[0]);
       if (c >= want) {
         LST(lock(0, want));
-        converged = true;
+        converged_ = true;
         break;
       }
       int win0 = 0;
       if (moving && c >= 2 * nb) {
         LST(lock(0, 2 * nb));
+        ++locks;
         win0 = 2 * nb;
         wv = std::min(w, d - win0);
       }
@@ -801,21 +868,22 @@ struct Solver {
         }
       if (na == 0) {  // everything in the window converged but not locked
         LST(lock(win0, std::min(wv, nev - ell)));
-        converged = ell >= nev;
-        if (converged) break;
+        ++locks;
+        converged_ = ell >= nev;
+        if (converged_) break;
+        if (locks >= max_locks) return LREP_OK;
         continue;
       }
       LCK(cudaMemcpyAsync(act_d, h->act, sizeof(int) * na, cudaMemcpyHostToDevice, st));
       LCK(cudaMemcpyAsync(lam_act, h->lam_act, sizeof(double) * na, cudaMemcpyHostToDevice, st));
       LST(step5_6_7(win0, wv, end, na));
       if (d == 0) return p->fail(LREP_ERR_BREAKDOWN, "search space collapsed");
+      if (locks >= max_locks) return LREP_OK;
     }
-    p->iters = std::min(it, maxit);
+    *ended = true;
+    p->iters = std::min(it_, maxit);
     LST(finalize());
-    if (events) {
-      // nothing: phase times were accumulated per iteration
-    }
-    return converged ? LREP_OK : LREP_NOT_CONVERGED;
+    return converged_ ? LREP_OK : LREP_NOT_CONVERGED;
   }
 
   lrep_status step5_6_7(int win0, int wv, int end, int na) {
@@ -831,7 +899,10 @@ struct Solver {
       pj.Xh = Xh; pj.Yh = Yh; pj.ld = dmax; pj.d = d; pj.end = end;
       pj.w_prev = w_prev; pj.na = na; pj.act = act_d; pj.Ph = Ph; pj.Qh = Qh;
       pj.ldo = dmax; pj.work = pqwork; pj.count = cnt_d + 1; pj.tau = p->opts.discard_tol;
-      LCK(small_pq(pj, st));
+      LST(timed(LREP_PC_SMALL, [&] {
+        LCK(small_pq(pj, st));
+        return LREP_OK;
+      }));
       LCK(cudaMemcpyAsync(&h->cnt[1], cnt_d + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     } else {
       h->cnt[1] = 0;
@@ -846,14 +917,20 @@ struct Solver {
     for (int sweep = 0; sweep < std::max(1, p->opts.ngs); ++sweep) {
       // M Z = W Lambda + (X~ Lambda - M Y~); generalized: B W, B X~
       if (gen && sweep) LST(apply(LREP_OP_B, na, Wsol, BT));
-      LCK(gather_combine(n, na, act_d, lam_act, bux(t), -1.0, TM, sweep ? lam_act : nullptr,
-                         sweep ? (gen ? BT : Wsol) : nullptr, ld, Rhs, ld, st));
+      LST(timed(LREP_PC_OTHER, [&] {
+        LCK(gather_combine(n, na, act_d, lam_act, bux(t), -1.0, TM, sweep ? lam_act : nullptr,
+                           sweep ? (gen ? BT : Wsol) : nullptr, ld, Rhs, ld, st));
+        return LREP_OK;
+      }));
       LST(cg_solve(LREP_OP_M, na, Rhs, Zsol, p->opts.cg_tol, p->opts.cg_maxit, 0, cgop));
       // K W = Z Lambda + (Y~ Lambda - K X~), projected onto range(K);
       // generalized: B Z, B Y~
       if (gen) LST(apply(LREP_OP_B, na, Zsol, BT));
-      LCK(gather_combine(n, na, act_d, lam_act, bvy(t), -1.0, TK, lam_act, gen ? BT : Zsol, ld,
-                         Rhs, ld, st));
+      LST(timed(LREP_PC_OTHER, [&] {
+        LCK(gather_combine(n, na, act_d, lam_act, bvy(t), -1.0, TK, lam_act, gen ? BT : Zsol,
+                           ld, Rhs, ld, st));
+        return LREP_OK;
+      }));
       if (r > 0) {
         LST(gram(seg1(Q0, ld, r), seg1(Rhs, ld, na), Cproj, r));
         LST(update(na, 1.0, seg1(Q0, ld, r), Cproj, r, -1.0, Rhs));
@@ -871,8 +948,11 @@ struct Solver {
       diag_copy_kernel<<<1, 64, 0, st>>>(na, G2, na, refz2); LREP_COUNT_LAUNCH();
       LCK(cudaGetLastError());
     } else {
-      LCK(colnorm2_f64(n, na, Wsol, ld, refw2, part, counters + 1, st));
-      LCK(colnorm2_f64(n, na, Zsol, ld, refz2, part, counters + 1, st));
+      LST(timed(LREP_PC_OTHER, [&] {
+        LCK(colnorm2_f64(n, na, Wsol, ld, refw2, part, counters + 1, st));
+        LCK(colnorm2_f64(n, na, Zsol, ld, refz2, part, counters + 1, st));
+        return LREP_OK;
+      }));
     }
     // P~ = U P^, Q~ = V Q^ and their products by the same combinations
     LCK(cudaEventSynchronize(evp));
@@ -1008,31 +1088,88 @@ size_t bosp_footprint(lrep_problem p, int nev, int nb) {
   return S.bytes_needed();
 }
 
-lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol, SmallBatcher* batcher) {
+// A solve in progress (lrep_solve_begin / lrep_solve_advance): the solver
+// lives on the heap between calls and owns its pinned mirror and events.
+struct ActiveSolve {
   Solver S{};
+};
+
+void bosp_abort(lrep_problem p) {
+  if (!p->active) return;
+  ActiveSolve* a = static_cast<ActiveSolve*>(p->active);
+  a->S.release_host();
+  delete a;
+  p->active = nullptr;
+}
+
+static lrep_status bosp_end(lrep_problem p, lrep_status s, int nev) {
+  bosp_abort(p);
+  p->solved = (s == LREP_OK || s == LREP_NOT_CONVERGED);
+  p->nev_solved = nev;
+  return s;
+}
+
+lrep_status bosp_begin(lrep_problem p, int nev, int nb, double tol, SmallBatcher* batcher) {
+  bosp_abort(p);
+  ActiveSolve* a = new ActiveSolve();
+  Solver& S = a->S;
   configure(S, p, nev, nb, tol);
   S.batcher = batcher;
   for (double& v : p->prof) v = 0.0;
   for (double& v : p->prof_cg) v = 0.0;
-  if (S.dmax > 256) return p->fail(LREP_ERR_ARG, "window + 2*block exceeds 256 columns");
-  if (S.nb > 64) return p->fail(LREP_ERR_ARG, "block exceeds 64");
-  if ((int64_t)S.dmax > S.n - S.r) return p->fail(LREP_ERR_ARG, "n too small for nev/block");
+  for (double& v : p->prof_class) v = 0.0;
+  p->solved = false;
+  if (S.dmax > 256) {
+    delete a;
+    return p->fail(LREP_ERR_ARG, "window + 2*block exceeds 256 columns");
+  }
+  if (S.nb > 64) {
+    delete a;
+    return p->fail(LREP_ERR_ARG, "block exceeds 64");
+  }
+  if ((int64_t)S.dmax > S.n - S.r) {
+    delete a;
+    return p->fail(LREP_ERR_ARG, "n too small for nev/block");
+  }
   p->history.clear();
   p->iters = 0;
   p->matvecs = 0;
   p->rebiorths = 0;
+  p->nconv = 0;
   for (double& t : p->timings) t = 0.0;
+  p->active = a;
   lrep_status s = S.alloc();
   if (s == LREP_OK) {
     S.events = true;
     for (auto& e : S.ev)
       if (cudaEventCreate(&e) != cudaSuccess) S.events = false;
-    s = S.run();
+    s = S.begin();
   }
-  S.release_host();
-  p->solved = (s == LREP_OK || s == LREP_NOT_CONVERGED);
-  p->nev_solved = nev;
-  return s;
+  if (s != LREP_OK) return bosp_end(p, s, nev);
+  return LREP_OK;
+}
+
+lrep_status bosp_advance(lrep_problem p, int max_locks, bool* ended, int* locked) {
+  *ended = false;
+  *locked = 0;
+  if (!p->active) return p->fail(LREP_ERR_STATE, "no solve in progress (lrep_solve_begin)");
+  ActiveSolve* a = static_cast<ActiveSolve*>(p->active);
+  const int nev = a->S.nev;
+  bool done = false;
+  lrep_status s = a->S.iterate(max_locks < 1 ? 1 : max_locks, &done);
+  *locked = a->S.ell;
+  if (done || (s != LREP_OK && s != LREP_NOT_CONVERGED)) {
+    *ended = true;
+    return bosp_end(p, s, nev);
+  }
+  return LREP_OK;
+}
+
+lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol, SmallBatcher* batcher) {
+  LST(bosp_begin(p, nev, nb, tol, batcher));
+  bool ended = false;
+  int locked = 0;
+  return bosp_advance(p, 1 << 30, &ended, &locked);
 }
 
 }  // namespace lrep

@@ -317,6 +317,7 @@ lrep_status lrep_create_operator(lrep_problem* out, int64_t n, lrep_apply_fn fn,
 
 lrep_status lrep_set_mass_dense(lrep_problem p, const double* B, int64_t ld, int32_t mem) {
   if (!p) return LREP_ERR_ARG;
+  bosp_abort(p);  // a solve in progress ends with any change to the problem
   if (p->op.kind != OP_DENSE || !valid_mem(mem) || (B && ld < p->op.n))
     return p->fail(LREP_ERR_ARG, "lrep_set_mass_dense: dense problem and ld >= n required");
   const int64_t n = p->op.n;
@@ -347,6 +348,7 @@ lrep_status lrep_set_mass_dense(lrep_problem p, const double* B, int64_t ld, int
 lrep_status lrep_set_mass_csr(lrep_problem p, const int64_t* rowptr, const int32_t* colind,
                               const double* values, int32_t mem) {
   if (!p) return LREP_ERR_ARG;
+  bosp_abort(p);  // a solve in progress ends with any change to the problem
   if (p->op.kind != OP_CSR || !valid_mem(mem) || (rowptr && (!colind || !values)))
     return p->fail(LREP_ERR_ARG, "lrep_set_mass_csr: CSR problem and all three arrays required");
   const int64_t n = p->op.n;
@@ -380,6 +382,7 @@ lrep_status lrep_set_mass_csr(lrep_problem p, const int64_t* rowptr, const int32
 
 lrep_status lrep_set_mass_callback(lrep_problem p, int32_t enable) {
   if (!p) return LREP_ERR_ARG;
+  bosp_abort(p);  // a solve in progress ends with any change to the problem
   if (p->op.kind != OP_CALLBACK)
     return p->fail(LREP_ERR_ARG, "lrep_set_mass_callback: callback problem required");
   p->op.hasB = enable != 0;
@@ -389,6 +392,7 @@ lrep_status lrep_set_mass_callback(lrep_problem p, int32_t enable) {
 lrep_status lrep_set_nullspace(lrep_problem p, int32_t r, const double* X0,
                                const double* Y0, int64_t ld, int32_t mem) {
   if (!p) return LREP_ERR_ARG;
+  bosp_abort(p);  // a solve in progress ends with any change to the problem
   if (r < 0 || r > 64 || (r > 0 && (!X0 || ld < p->op.n)) || !valid_mem(mem))
     return p->fail(LREP_ERR_ARG, "lrep_set_nullspace: invalid argument (0 <= r <= 64)");
   p->r = r;
@@ -405,6 +409,7 @@ lrep_status lrep_find_nullspace(lrep_problem p, int32_t r_max, double tol, int32
                                 double* X0_out, int64_t ld_out, int32_t mem_out,
                                 int32_t* r_host, int32_t* iters_host) {
   if (!p) return LREP_ERR_ARG;
+  bosp_abort(p);  // a solve in progress ends with any change to the problem
   if (r_max < 0 || r_max > 60 || !(tol > 0.0) || !(tol < 1.0) || maxit < 1 || !r_host ||
       (X0_out && (ld_out < p->op.n ||
                   (mem_out != LREP_MEM_HOST && mem_out != LREP_MEM_DEVICE_COPY))))
@@ -427,6 +432,7 @@ lrep_status lrep_find_nullspace(lrep_problem p, int32_t r_max, double tol, int32
 
 lrep_status lrep_set_options(lrep_problem p, const lrep_options* o) {
   if (!p || !o) return LREP_ERR_ARG;
+  bosp_abort(p);  // a solve in progress ends with any change to the problem
   if (o->struct_size != (int32_t)sizeof(lrep_options))
     return p->fail(LREP_ERR_ARG, "lrep_set_options: struct_size mismatch");
   if (o->s < 2 || o->ngs < 1 || o->cg_maxit < 0 || !(o->cg_tol > 0.0) || o->maxit < 1 ||
@@ -448,6 +454,7 @@ lrep_status lrep_set_options(lrep_problem p, const lrep_options* o) {
 lrep_status lrep_set_start(lrep_problem p, int32_t ncols, const double* U0,
                            const double* V0, int64_t ld, int32_t mem) {
   if (!p) return LREP_ERR_ARG;
+  bosp_abort(p);  // a solve in progress ends with any change to the problem
   if (ncols < 0 || (ncols > 0 && (!U0 || !V0 || ld < p->op.n)) || !valid_mem(mem))
     return p->fail(LREP_ERR_ARG, "lrep_set_start: invalid argument");
   p->start_cols = ncols;
@@ -468,12 +475,36 @@ lrep_status lrep_solve(lrep_problem p, int32_t nev, int32_t block, double tol) {
   return bosp_solve(p, nev, block, tol);
 }
 
+lrep_status lrep_solve_begin(lrep_problem p, int32_t nev, int32_t block, double tol) {
+  if (!p) return LREP_ERR_ARG;
+  if (nev < 1 || block < 1 || !(tol > 0.0))
+    return p->fail(LREP_ERR_ARG, "lrep_solve_begin: nev, block >= 1 and tol > 0 required");
+  p->err.clear();
+  return bosp_begin(p, nev, block, tol);
+}
+
+lrep_status lrep_solve_advance(lrep_problem p, int32_t locks, int32_t* locked,
+                               int32_t* done) {
+  if (!p) return LREP_ERR_ARG;
+  if (locks < 1) return p->fail(LREP_ERR_ARG, "lrep_solve_advance: locks >= 1 required");
+  bool ended = false;
+  int nlocked = 0;
+  const lrep_status s = bosp_advance(p, locks, &ended, &nlocked);
+  if (locked) *locked = nlocked;
+  if (done) *done = ended ? 1 : 0;
+  return s;
+}
+
 lrep_status lrep_query(lrep_problem p, int32_t what, void* dst, int64_t dst_bytes,
                        int32_t mem) {
   if (!p || !dst || dst_bytes < 0) return LREP_ERR_ARG;
   if (mem != LREP_MEM_HOST && mem != LREP_MEM_DEVICE_COPY)
     return p->fail(LREP_ERR_ARG, "lrep_query: mem must be HOST or DEVICE_COPY");
-  if (!p->solved) return p->fail(LREP_ERR_STATE, "lrep_query before a solve");
+  // the profiles describe the work so far, also while a solve is in progress
+  const bool profile_query =
+      what == LREP_Q_PROFILE || what == LREP_Q_PROFILE_CG || what == LREP_Q_PROFILE_CLASSES;
+  if (!p->solved && !(profile_query && p->active))
+    return p->fail(LREP_ERR_STATE, "lrep_query before a solve");
   const int64_t n = p->op.n;
   const int nc = p->nconv;
   auto put = [&](const void* src, int64_t bytes, bool src_dev) -> lrep_status {
@@ -528,6 +559,7 @@ lrep_status lrep_query(lrep_problem p, int32_t what, void* dst, int64_t dst_byte
     case LREP_Q_REBIORTHS: { int32_t v = p->rebiorths; return put(&v, sizeof(v), false); }
     case LREP_Q_PROFILE: return put(p->prof, sizeof(p->prof), false);
     case LREP_Q_PROFILE_CG: return put(p->prof_cg, sizeof(p->prof_cg), false);
+    case LREP_Q_PROFILE_CLASSES: return put(p->prof_class, sizeof(p->prof_class), false);
     default: return p->fail(LREP_ERR_ARG, "lrep_query: unknown item");
   }
 }
@@ -541,6 +573,7 @@ lrep_status lrep_destroy(lrep_problem p) {
   if (!p) return LREP_ERR_ARG;
   if (p->stream) cudaStreamSynchronize(p->stream);
   else cudaDeviceSynchronize();
+  bosp_abort(p);
   free_split(p);
   for (void* q : p->op.owned) cudaFree(q);
   p->op.owned.clear();

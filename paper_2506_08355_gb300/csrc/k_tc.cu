@@ -211,6 +211,34 @@ __device__ __forceinline__ bool sym_next(int S, int C, int b, int T, int& i, int
   }
 }
 
+// tile cursor over a CTA's items (round-robin) and their tiles, in the
+// order every role of the kernel walks them
+struct SymCursor {
+  int q, S, C, i, j;
+  bool valid;
+  __device__ void start(int q0, int Tsb, int b, int T, int items) {
+    q = q0;
+    valid = false;
+    while (q < items) {
+      sym_item(q, Tsb, S, C);
+      i = 0;
+      j = -1;
+      if (sym_next(S, C, b, T, i, j)) {
+        valid = true;
+        return;
+      }
+      q += gridDim.x;
+    }
+  }
+  __device__ void next(int Tsb, int b, int T, int items) {
+    if (!valid) return;
+    if (sym_next(S, C, b, T, i, j)) return;
+    start(q + gridDim.x, Tsb, b, T, items);
+  }
+};
+
+constexpr int SYM_PREFETCH = 3;  // tiles prefetched into L2 ahead of their load
+
 template <int N>
 __global__ void __launch_bounds__(192, 1)
 bf16x3_sym_kernel(const __grid_constant__ CUtensorMap mAhi,
@@ -256,41 +284,50 @@ bf16x3_sym_kernel(const __grid_constant__ CUtensorMap mAhi,
   if (warp == 0) {
     if (lane == 0) {  // TMA producer: every tile of this CTA's items in order
       int it = 0;
-      bool stop = false;
-      for (int q = blockIdx.x; q < items && !stop; q += gridDim.x) {
-        int S, C;
-        sym_item(q, Tsb, S, C);
-        int i = 0, j = -1;
-        while (sym_next(S, C, b, T, i, j)) {
-          const int sidx = it % SYM_STAGES;
-          if (it >= SYM_STAGES &&
-              !mbar_wait(smem_u32(&empty[sidx]), ((it / SYM_STAGES) - 1) & 1, err, 21)) {
-            stop = true;
-            break;
-          }
-          if (*(volatile int*)err) {
-            stop = true;
-            break;
-          }
-          uint8_t* st = base + sidx * STAGE;
-          const uint32_t fb = smem_u32(&full[sidx]);
-          mbar_expect_tx(fb, (uint32_t)STAGE);
-          const int I = (S * b + i) * SYM_TILE, J = (C * b + j) * SYM_TILE;
-          tma_load_2d(smem_u32(st), &mAhi, fb, J, I);
-          tma_load_2d(smem_u32(st + SYM_BOX), &mAhi, fb, J + BK, I);
-          tma_load_2d(smem_u32(st + 2 * SYM_BOX), &mAlo, fb, J, I);
-          tma_load_2d(smem_u32(st + 3 * SYM_BOX), &mAlo, fb, J + BK, I);
-          uint8_t* xs = st + 4 * SYM_BOX;
-          tma_load_2d(smem_u32(xs), &mXhi, fb, J, 0);
-          tma_load_2d(smem_u32(xs + XBOX), &mXhi, fb, J + BK, 0);
-          tma_load_2d(smem_u32(xs + 2 * XBOX), &mXlo, fb, J, 0);
-          tma_load_2d(smem_u32(xs + 3 * XBOX), &mXlo, fb, J + BK, 0);
-          tma_load_2d(smem_u32(xs + 4 * XBOX), &mXhi, fb, I, 0);
-          tma_load_2d(smem_u32(xs + 5 * XBOX), &mXhi, fb, I + BK, 0);
-          tma_load_2d(smem_u32(xs + 6 * XBOX), &mXlo, fb, I, 0);
-          tma_load_2d(smem_u32(xs + 7 * XBOX), &mXlo, fb, I + BK, 0);
-          ++it;
+      SymCursor cur, pre;
+      cur.start(blockIdx.x, Tsb, b, T, items);
+      pre = cur;
+      // the first tiles' operator boxes go to L2 ahead of their loads
+      for (int k = 0; k < SYM_PREFETCH && pre.valid; ++k) {
+        const int I = (pre.S * b + pre.i) * SYM_TILE, J = (pre.C * b + pre.j) * SYM_TILE;
+        tma_prefetch_2d(&mAhi, J, I);
+        tma_prefetch_2d(&mAhi, J + BK, I);
+        tma_prefetch_2d(&mAlo, J, I);
+        tma_prefetch_2d(&mAlo, J + BK, I);
+        pre.next(Tsb, b, T, items);
+      }
+      for (; cur.valid; cur.next(Tsb, b, T, items)) {
+        const int sidx = it % SYM_STAGES;
+        if (it >= SYM_STAGES &&
+            !mbar_wait(smem_u32(&empty[sidx]), ((it / SYM_STAGES) - 1) & 1, err, 21))
+          break;
+        if (*(volatile int*)err) break;
+        if (pre.valid) {
+          const int I = (pre.S * b + pre.i) * SYM_TILE, J = (pre.C * b + pre.j) * SYM_TILE;
+          tma_prefetch_2d(&mAhi, J, I);
+          tma_prefetch_2d(&mAhi, J + BK, I);
+          tma_prefetch_2d(&mAlo, J, I);
+          tma_prefetch_2d(&mAlo, J + BK, I);
+          pre.next(Tsb, b, T, items);
         }
+        uint8_t* st = base + sidx * STAGE;
+        const uint32_t fb = smem_u32(&full[sidx]);
+        mbar_expect_tx(fb, (uint32_t)STAGE);
+        const int I = (cur.S * b + cur.i) * SYM_TILE, J = (cur.C * b + cur.j) * SYM_TILE;
+        tma_load_2d(smem_u32(st), &mAhi, fb, J, I);
+        tma_load_2d(smem_u32(st + SYM_BOX), &mAhi, fb, J + BK, I);
+        tma_load_2d(smem_u32(st + 2 * SYM_BOX), &mAlo, fb, J, I);
+        tma_load_2d(smem_u32(st + 3 * SYM_BOX), &mAlo, fb, J + BK, I);
+        uint8_t* xs = st + 4 * SYM_BOX;
+        tma_load_2d(smem_u32(xs), &mXhi, fb, J, 0);
+        tma_load_2d(smem_u32(xs + XBOX), &mXhi, fb, J + BK, 0);
+        tma_load_2d(smem_u32(xs + 2 * XBOX), &mXlo, fb, J, 0);
+        tma_load_2d(smem_u32(xs + 3 * XBOX), &mXlo, fb, J + BK, 0);
+        tma_load_2d(smem_u32(xs + 4 * XBOX), &mXhi, fb, I, 0);
+        tma_load_2d(smem_u32(xs + 5 * XBOX), &mXhi, fb, I + BK, 0);
+        tma_load_2d(smem_u32(xs + 6 * XBOX), &mXlo, fb, I, 0);
+        tma_load_2d(smem_u32(xs + 7 * XBOX), &mXlo, fb, I + BK, 0);
+        ++it;
       }
       counts[0] = it;
     }

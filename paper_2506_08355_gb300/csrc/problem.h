@@ -108,10 +108,14 @@ struct lrep_problem_s {
   // operator-product profile (options.profile)
   double prof[4] = {0, 0, 0, 0};
   double prof_cg[4] = {0, 0, 0, 0};  // CG-operator products alone
+  double prof_class[2 * LREP_PC_COUNT] = {};  // (seconds, spans) per LREP_PC_* class
   // scratch for op-level calls on this problem
   lrep::Arena op_arena;
   // solver workspace (kept between solves of the same shape)
   lrep::Arena ws;
+  // a solve in progress between lrep_solve_begin and its last
+  // lrep_solve_advance (bosp.cu), else null
+  void* active = nullptr;
   size_t ws_key[4] = {0, 0, 0, 0};
 
   lrep_status fail(lrep_status st, const std::string& msg) {
@@ -144,6 +148,12 @@ struct SmallBatcher {
 };
 lrep_status bosp_solve(lrep_problem p, int nev, int nb, double tol,
                        SmallBatcher* batcher = nullptr);
+// the same solve in steps: begin (Steps 1-2), then advance by lock events
+// until *ended; abort drops a solve in progress
+lrep_status bosp_begin(lrep_problem p, int nev, int nb, double tol,
+                       SmallBatcher* batcher = nullptr);
+lrep_status bosp_advance(lrep_problem p, int max_locks, bool* ended, int* locked);
+void bosp_abort(lrep_problem p);
 // device bytes the solver's workspace needs for (nev, nb) on p
 size_t bosp_footprint(lrep_problem p, int nev, int nb);
 // orthonormal basis of N(K) by LOBPCG (nullspace.cu); sets p->r, p->X0in

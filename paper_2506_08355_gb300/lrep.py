@@ -24,7 +24,8 @@ FORM_AB, FORM_KM = 0, 1
 OP_K, OP_M, OP_B = 0, 1, 2
 PREC_FP64, PREC_MIXED_BF16X3, PREC_FP64_SLICED, PREC_MIXED_SLICED = 0, 1, 2, 3
 (Q_NCONV, Q_EIGVALS, Q_X, Q_Y, Q_U, Q_V, Q_RESID, Q_ITERS, Q_MATVECS, Q_TIMINGS,
- Q_BIORTH_ERR, Q_HISTORY, Q_REBIORTHS, Q_PROFILE, Q_PROFILE_CG) = range(15)
+ Q_BIORTH_ERR, Q_HISTORY, Q_REBIORTHS, Q_PROFILE, Q_PROFILE_CG, Q_PROFILE_CLASSES) = range(16)
+PROFILE_CLASSES = ("prod_cg", "prod_f64", "gram", "update", "small", "cg_vec", "alg1", "other")
 
 
 class Options(C.Structure):
@@ -68,6 +69,9 @@ EXPORTS = {
     "lrep_set_start": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.c_int64, C.c_int32]),
     "lrep_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double]),
+    "lrep_solve_begin": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_double]),
+    "lrep_solve_advance": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32)]),
     "lrep_query": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32]),
     "lrep_last_error": (C.c_char_p, [C.c_void_p]),
     "lrep_destroy": (C.c_int, [C.c_void_p]),
@@ -349,6 +353,19 @@ class Problem:
     def solve(self, nev, block, tol):
         return _check(lib().lrep_solve(self.h, nev, block, tol), self.h)
 
+    def solve_begin(self, nev, block, tol):
+        """Start a solve to be advanced batch by batch (lrep_solve_begin)."""
+        return _check(lib().lrep_solve_begin(self.h, nev, block, tol), self.h)
+
+    def solve_advance(self, locks=1):
+        """Run outer iterations until `locks` more lock events or the end of
+        the solve (lrep_solve_advance); returns (status, pairs locked so far,
+        done)."""
+        done, locked = C.c_int32(), C.c_int32()
+        st = _check(lib().lrep_solve_advance(self.h, locks, C.byref(locked), C.byref(done)),
+                    self.h)
+        return st, locked.value, bool(done.value)
+
     # results -------------------------------------------------------------
     def _q_scalar(self, what, ctype):
         v = ctype()
@@ -414,6 +431,13 @@ class Problem:
     def profile_cg(self):
         """profile() restricted to the CG-operator products."""
         return self._q_array(Q_PROFILE_CG, 4)
+
+    def profile_classes(self):
+        """{class: (device seconds, timed spans)} of the last profiled solve
+        (options.profile), classes as in PROFILE_CLASSES."""
+        v = self._q_array(Q_PROFILE_CLASSES, 2 * len(PROFILE_CLASSES))
+        return {name: (float(v[2 * i]), int(v[2 * i + 1]))
+                for i, name in enumerate(PROFILE_CLASSES)}
 
     # op level --------------------------------------------------------------
     def apply(self, op, X, Y, cg=False):

@@ -257,3 +257,40 @@ def test_full_size_stencil_64cubed_fp64(L):
     lam, X, Y = check(op, prob, lam_ref, 1e-10, 32, rtol=1e-10)
     assert np.abs(p["X0"][:, 0] @ Y).max() < 1e-9
     prob.close()
+
+
+def test_solve_in_batches_equals_solve(L):
+    """lrep_solve_begin + lrep_solve_advance (one lock event per call)
+    reproduce lrep_solve exactly: same iterations, bitwise-equal
+    eigenvalues and vectors (the solver's reductions have a fixed order).
+    nev = 24 in windows of nb = 4 locks 2 nb = 8 pairs at a time, so the
+    solve ends within four calls; querying mid-solve is a state error."""
+    p = synth.haar_dense(600, seed=7, n_zero_k=2)
+    op = R.DenseOp(p["K"], p["M"])
+    lam_r, _, _ = R.lrep_definition(p["K"], p["M"], 24, r=2)
+    whole = L.Problem.dense(p["K"], p["M"])
+    whole.set_nullspace(p["X0"])
+    assert whole.solve(24, 4, 1e-10) == L.OK
+    steps = L.Problem.dense(p["K"], p["M"])
+    steps.set_nullspace(p["X0"])
+    steps.solve_begin(24, 4, 1e-10)
+    with pytest.raises(L.LrepError):
+        steps.eigvals()
+    calls, done, st, locked = 0, False, None, 0
+    while not done:
+        st, now, done = steps.solve_advance(1)
+        assert now > locked and (done or now % 8 == 0), (now, locked)
+        locked = now
+        calls += 1
+        assert calls <= 5
+    assert locked == 24
+    assert st == L.OK and 3 <= calls <= 4
+    assert steps.iters() == whole.iters()
+    np.testing.assert_array_equal(steps.eigvals(), whole.eigvals())
+    np.testing.assert_array_equal(steps.vectors(), whole.vectors())
+    check(op, steps, lam_r, 1e-10, 24)
+    # advancing with no solve in progress is a state error
+    with pytest.raises(L.LrepError):
+        steps.solve_advance(1)
+    whole.close()
+    steps.close()
