@@ -36,6 +36,19 @@ lrep_status lrep_op_apply_cg(lrep_problem p, int32_t op, int32_t ncols,
                              const double* X, int64_t ldx, double* Y,
                              int64_t ldy);
 
+/* Step 6 inner solve (eq. block_GS and the text after it): one CG per
+ * column for op * X = B (op = LREP_OP_K or LREP_OP_M), zero start, the
+ * problem's CG operator (as lrep_op_apply_cg), the solver's own kernels.
+ * Column j stops once ||r_j||_2 <= tol ||b_j||_2; the block stops after
+ * maxit iterations or when every column has stopped.  B: n x ncols device
+ * block (ldb >= n), X: n x ncols device output (ldx >= n), 1 <= ncols <= 64,
+ * maxit >= 0.  *iters (host, may be NULL): iterations in which at least
+ * one column was still active.  Runs on the problem's stream and
+ * synchronises it. */
+lrep_status lrep_op_cg(lrep_problem p, int32_t op, int32_t ncols, const double* B,
+                       int64_t ldb, double* X, int64_t ldx, double tol, int32_t maxit,
+                       int32_t* iters);
+
 /* Tall-skinny Gram G = A^T B (A n x a, B n x b), the inner products of
  * eq. hat_H (K^ = U^T K U, M^ = V^T M V) and eq. update_W/Z.  G is a x b
  * with leading dimension ldg.  Deterministic (fixed reduction order). */

@@ -616,6 +616,58 @@ lrep_status lrep_op_apply_cg(lrep_problem p, int32_t op, int32_t ncols, const do
   return s;
 }
 
+lrep_status lrep_op_cg(lrep_problem p, int32_t op, int32_t ncols, const double* B,
+                       int64_t ldb, double* X, int64_t ldx, double tol, int32_t maxit,
+                       int32_t* iters) {
+  if (!p) return LREP_ERR_ARG;
+  const int64_t n = p->op.n;
+  if (!B || !X || ncols < 1 || ncols > 64 || ldb < n || ldx < n || maxit < 0 ||
+      !(tol >= 0.0) || (op != LREP_OP_K && op != LREP_OP_M))
+    return p->fail(LREP_ERR_ARG, "lrep_op_cg: invalid argument");
+  bosp_abort(p);
+  const size_t blk = (size_t)ldx * ncols;
+  const size_t aws = apply_ws_elems(p, ncols);
+  const size_t need = 3 * blk + cg_part_elems(n, ncols) + aws + 8 * (size_t)ncols + 4096;
+  if (p->op_arena.cap < need * sizeof(double))
+    PCK(p, p->op_arena.reserve(need * sizeof(double), p->stream));
+  Arena& A = p->op_arena;
+  A.off = 0;
+  double* R = A.take<double>(blk);
+  double* P = A.take<double>(blk);
+  double* Q = A.take<double>(blk);
+  CgState cg{};
+  cg.rho = A.take<double>(ncols);
+  cg.stop = A.take<double>(ncols);
+  cg.alpha = A.take<double>(ncols);
+  cg.beta = A.take<double>(ncols);
+  cg.active = A.take<int>(ncols);
+  cg.done = A.take<int>(8);
+  cg.iters = A.take<int>(8);
+  cg.counter = A.take<unsigned int>(8);
+  cg.part = A.take<double>(cg_part_elems(n, ncols));
+  double* ws = A.take<double>(aws + 1);
+  if (!ws) return p->fail(LREP_ERR_NOMEM, "lrep_op_cg: workspace layout overflow");
+  PCK(p, cudaMemsetAsync(cg.done, 0, 8 * sizeof(int), p->stream));
+  PCK(p, cudaMemsetAsync(cg.iters, 0, 8 * sizeof(int), p->stream));
+  PCK(p, cudaMemsetAsync(cg.counter, 0, 8 * sizeof(unsigned int), p->stream));
+  PCK(p, cg_init(n, ncols, B, ldb, X, R, P, ldx, tol, cg, p->stream));
+  for (int it = 0; it < maxit; ++it) {
+    const lrep_status s = apply_op_cg(p, op, ncols, P, ldx, Q, ldx, cg.done, ws, aws);
+    if (s != LREP_OK) return s;
+    PCK(p, cg_alpha(n, ncols, P, Q, ldx, cg, p->stream));
+    PCK(p, cg_update(n, ncols, X, R, P, Q, ldx, cg, p->stream));
+    PCK(p, cg_pdir(n, ncols, R, P, ldx, cg, p->stream));
+  }
+  int h[2] = {0, 0};
+  PCK(p, cudaMemcpyAsync(h, cg.iters, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  if (p->op.tc_err)
+    PCK(p, cudaMemcpyAsync(h + 1, p->op.tc_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  PCK(p, cudaStreamSynchronize(p->stream));
+  if (h[1]) return p->fail(LREP_ERR_CUDA, "tensor-core pipeline wait expired");
+  if (iters) *iters = h[0];
+  return LREP_OK;
+}
+
 lrep_status lrep_op_gram(int64_t n, int32_t a, int32_t b, const double* A, int64_t lda,
                          const double* B, int64_t ldb, double* G, int64_t ldg,
                          void* stream) {

@@ -121,6 +121,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b,
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+// same, always accumulating into D
+__device__ __forceinline__ void mma_bf16_acc(uint32_t dtmem, uint64_t a, uint64_t b,
+                                             uint32_t idesc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.eq.u32 p, 1, 1;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc));
+}
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    mbar)

@@ -92,6 +92,9 @@ EXPORTS = {
                                 C.c_void_p, C.c_int64]),
     "lrep_op_apply_cg": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
                                    C.c_void_p, C.c_int64]),
+    "lrep_op_cg": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                             C.c_void_p, C.c_int64, C.c_double, C.c_int32,
+                             C.POINTER(C.c_int32)]),
     "lrep_op_gram": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
                                C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p]),
     "lrep_op_update": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
@@ -444,6 +447,14 @@ class Problem:
         """Y = op(X) for device blocks X, Y (torch (c, ld))."""
         f = lib().lrep_op_apply_cg if cg else lib().lrep_op_apply
         _check(f(self.h, op, X.shape[0], _ptr(X), _ld(X), _ptr(Y), _ld(Y)), self.h)
+
+    def cg(self, op, B, X, tol, maxit):
+        """X <- CG solution of op X = B (device blocks (c, ld)), zero start,
+        the problem's CG operator (lrep_op_cg); returns the iterations run."""
+        it = C.c_int32()
+        _check(lib().lrep_op_cg(self.h, op, B.shape[0], _ptr(B), _ld(B), _ptr(X), _ld(X),
+                                tol, maxit, C.byref(it)), self.h)
+        return it.value
 
     def close(self):
         if self.h:

@@ -252,3 +252,36 @@ def test_bf16x3_tensor_core_product(L, n, c):
         # and it is not the float64 path: the error is visibly non-zero
         assert err.max() > 1e-12
     p.close()
+
+
+@pytest.mark.parametrize("prec_name", ["PREC_FP64", "PREC_FP64_SLICED"])
+def test_cg_matches_oracle_columnwise(L, prec_name):
+    """The CG of eq. block_GS (lrep_op_cg: the solver's cg_init / cg_alpha /
+    cg_update / cg_pdir kernels and its CG operator) against the oracle's
+    cg, column by column: at fixed iteration counts with no stopping, and
+    with the paper's tolerance 1e-2 (per-column stops, same iteration
+    count).  A zero right-hand side stays inactive on both sides.  Float64
+    products: the iterates agree to rounding amplified by the few steps
+    (bound 1e-11 relative to the column's norm)."""
+    from oracle import lrep_ref as R
+    n, c = 3000, 12
+    rng = np.random.default_rng(77)
+    p = synth.haar_dense(n, seed=77)
+    K, M = p["K"], p["M"]
+    B = rng.standard_normal((n, c))
+    B[:, 5] = 0.0
+    prob = L.Problem.dense(K, M)
+    prob.set_options(precision=getattr(L, prec_name))
+    Bd = to_dev(B)
+    Xd = L.device_block(n, c)
+    for op, mat in ((L.OP_K, K), (L.OP_M, M)):
+        for tol, maxit in ((0.0, 1), (0.0, 5), (0.0, 12), (1e-2, 60)):
+            its = prob.cg(op, Bd, Xd, tol, maxit)
+            X = from_dev(Xd)
+            Xr, its_r = R.cg(lambda Z: mat @ Z, B, tol, maxit)
+            assert its == its_r, (op, tol, maxit, its, its_r)
+            scale = np.maximum(np.linalg.norm(Xr, axis=0), 1e-300)
+            err = np.linalg.norm(X - Xr, axis=0) / scale
+            assert err.max() < 1e-11, (op, tol, maxit, err.max())
+            assert np.all(X[:, 5] == 0.0)
+    prob.close()
