@@ -90,7 +90,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--op", default=None, choices=["dense", "tc", "sliced", "small", "stencil",
-                                                  "spectral", "spectral32", "gram", "nullspace"],
+                                                  "stencil32", "spectral", "spectral32", "gram",
+                                                  "nullspace"],
                     help="time one hot-path step alone (for ncu captures) instead of solves")
     ap.add_argument("--n", type=int, default=8192, help="order for --op")
     ap.add_argument("--cols", type=int, default=16, help="block columns for --op")
@@ -435,20 +436,28 @@ def op_mode(args):
         work = {"flops": 2.0 * n * n * c * mult, "fp64_flops": 2.0 * n * n * c,
                 "bytes": per * n * n + 16.0 * n * c, "max_rel_err": err}
         p.close()
-    elif args.op == "stencil":
+    elif args.op in ("stencil", "stencil32"):
+        # --n is the grid edge; stencil32: the float32 CG product.  X and Y
+        # are four times larger than L2 together unless the grid is small
         from paper_2506_08355_gb300 import synth
         s = synth.bdg_stencil(args.n)
         nn = s["n"]
         p = lrep.Problem.stencil(s["nx"], s["ny"], s["nz"], s["h"], -0.5, s["dK"], s["dM"])
+        f32 = args.op == "stencil32"
+        if f32:
+            p.set_options(precision=lrep.PREC_MIXED_BF16X3)
         X = torch.randn(c, nn, dtype=torch.float64, device="cuda", generator=g)
         Y = torch.empty(c, nn, dtype=torch.float64, device="cuda")
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         for _ in range(args.reps):
+            flush.zero_()  # 256 MB written: L2 holds none of X, Y, d at the start
             ev[0].record()
-            p.apply(lrep.OP_K, X, Y)
+            p.apply(lrep.OP_K, X, Y, cg=f32)
             ev[1].record()
             torch.cuda.synchronize()
             times.append(ev[0].elapsed_time(ev[1]))
-        work = {"flops": 9.0 * nn * c, "bytes": (16.0 * c + 8.0) * nn}
+        work = {"flops": 9.0 * nn * c, "bytes": (16.0 * c + 8.0) * nn,
+                "arith": "float32" if f32 else "float64", "l2": "flushed before each launch"}
         p.close()
     elif args.op in ("spectral", "spectral32"):
         N = args.n
@@ -625,7 +634,10 @@ def serve_mode(args):
         pr.close()
     line = {"metric": "serving: eigenpairs/s and latency at residual<=1e-8 (mixed path)",
             "value": total_nev / makespan, "unit": "eigenpairs/s", "n_gpus": 1,
-            "higher_is_better": True, "p50_ms": float(np.percentile(lat, 50)),
+            "steps": 1, "warmup": 0, "ms_per_step": makespan * 1e3,
+            "step": "the whole trace (makespan from the first arrival to the last result)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
             "requests": len(probs), "ok": ok, "failed_examples": failed,
             "makespan_s": makespan,
@@ -635,7 +647,9 @@ def serve_mode(args):
             "dtype": "bf16x3+f64", "data": "synthetic",
             "config": {"workload": "serving-poisson200-dense-n256-4096-nev4-32-tol1e-8",
                        "pool": args.pool, "pool_generation_s": t_gen,
-                       "arrivals": "Poisson, mean 200/s (seed 4)"}}
+                       "arrivals": "Poisson, mean 200/s (seed 4)",
+                       "admission": "smallest HBM footprint first within the budget "
+                                    "(a request passed over 64 times goes first)"}}
     print(json.dumps(line), flush=True)
 
 
@@ -704,7 +718,9 @@ KERNELS = {  # the kernels behind each profiled class of solver work
 def product_kernel_names(config, prec, nb):
     import paper_2506_08355_gb300.lrep as lrep
     if config == 2:
-        return "stencil_kernel (2.5-D)", "stencil_kernel (2.5-D)"
+        cg = ("stencil_kernel<float> (2.5-D)" if prec & lrep.PREC_MIXED_BF16X3
+              else "stencil_kernel<double> (2.5-D)")
+        return cg, "stencil_kernel<double> (2.5-D)"
     if config == 5:
         cg = ("spectral_axis_kernel<float> x 3 axes" if prec & lrep.PREC_MIXED_BF16X3
               else "spectral_axis_kernel<double> x 3 axes")
@@ -712,8 +728,7 @@ def product_kernel_names(config, prec, nb):
     f64 = ("oz_gemm_kernel (+ X digit planes, split-K sum)" if prec & lrep.PREC_FP64_SLICED
            else "dense_apply_kernel (+ split-K reduce)")
     if prec & lrep.PREC_MIXED_BF16X3:
-        cg = ("bf16x3_sym_kernel (upper tiles; + X split, fixed-order reduce)" if nb <= 32
-              else "bf16x3_kernel (+ X split, split-K sum)")
+        cg = "bf16x3_kernel (+ X split, split-K sum)"
     else:
         cg = f64
     return cg, f64
@@ -782,7 +797,8 @@ def profile_roofline(args, p, prob, lrep, stream, prec, nev, nb, tol, base, batc
     bytes_launch = prof[3] / launches
     hbm_peak = measured_peaks().get("hbm_gbs", 6780.7)
     kname = names[cls]
-    alu = kname.startswith("dense_apply") or kname.startswith("spectral_axis_kernel<double>")
+    alu = (kname.startswith("dense_apply") or kname.startswith("spectral_axis_kernel<double>")
+           or kname.startswith("stencil_kernel<double>"))
     roof = {"kernel": kname, "class": cls, "dominant_class": dom,
             "algorithmic_flops_per_launch": flops_launch,
             "algorithmic_bytes_per_launch": bytes_launch,
@@ -817,8 +833,6 @@ def compare_paths(args, p, prob, lrep, stream, prec, nev, nb, tol, base, iters):
     if cmp_name == "none" or cmp_name == args.precision:
         return None, None
     cprec = PRECISIONS[cmp_name]
-    if (cprec & PRECISIONS["mixed"]) and args.config == 2:
-        return None, None
     prob.set_options(precision=cprec, profile=0, **base)
     if args.config != 3:
         for _ in range(3):

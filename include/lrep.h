@@ -64,13 +64,14 @@ enum { LREP_FORM_AB = 0, LREP_FORM_KM = 1 };
  * lrep_set_mass_callback was called). */
 enum { LREP_OP_K = 0, LREP_OP_M = 1, LREP_OP_B = 2 };
 /* Arithmetic of the float64-accurate work and of the CG products (two
- * independent bits; bit 0 needs a dense or a spectral operator).
+ * independent bits; bit 0 needs a dense, stencil or spectral operator).
  * FP64: every product in float64 (FP64 FMA units).
  * MIXED_BF16X3 (bit 0): the inexact CG products of eq. block_GS use K, M
  *   split as hi + lo bfloat16 pairs (three bf16 tensor-core products, fp32
  *   accumulation); every product that enters H^ (eq. hat_H) and every
  *   residual (eq. tol) keeps float64 accuracy.  Spectral operators: the CG
- *   products run their transforms in float32 instead.
+ *   products run their transforms in float32 instead; stencil operators
+ *   their 7-point sums (float64 loads and stores).
  * FP64_SLICED (bit 1): the float64-accurate dense products (and, without
  *   bit 0, the CG products too) and, for every operator kind, the large
  *   tall-skinny Grams and block updates of the solve run on the bf16 tensor
@@ -304,11 +305,15 @@ const char* lrep_last_error(lrep_problem p);
 lrep_status lrep_destroy(lrep_problem p);
 
 /* ---- serving: continuous batching of concurrent solves ----------------
- * A server owns a host thread that advances every admitted request by one
- * BOSP iteration per step, batching the small projected problems of all
- * admitted requests into one launch.  Requests are admitted in arrival
- * order while their HBM footprint fits hbm_budget_bytes and a slot is
- * free.  The problems passed to submit must stay alive until wait returns.
+ * A server owns max_slots host threads, each running one admitted solve at
+ * a time on its own CUDA stream, so the device work of concurrent requests
+ * overlaps; the small projected problems of order < 40 of the running
+ * solves are batched into shared launches.  When a slot is free, the
+ * queued request with the smallest HBM footprint that fits
+ * hbm_budget_bytes next to the running solves starts (a request passed
+ * over 64 times goes first once it fits, and nothing overtakes it while it
+ * waits).  The problems passed to submit must stay alive until wait
+ * returns.
  */
 /* Device bytes a solve of (nev, block) on p needs beyond the operator
  * itself (solver workspace, plus the bf16 operator split in mixed mode when

@@ -462,9 +462,7 @@ struct Solver {
       nnz = (double)n * n;
       const int prec = p->opts.precision;
       if (cgop && (prec & LREP_PREC_MIXED_BF16X3))
-        // hi + lo bf16; up to 32 columns the symmetric kernel needs only the
-        // tiles on and above the diagonal
-        opbytes = (c <= 32 ? 2.0 : 4.0) * nnz;
+        opbytes = 4.0 * nnz;   // hi + lo bf16
       else if (prec & LREP_PREC_FP64_SLICED)
         opbytes = 14.0 * nnz;  // 7 bf16 digit planes
       else
@@ -776,6 +774,29 @@ struct Solver {
                     st));
       LCK(copy_cols(n, count, BV[t] + (int64_t)first * ld, ld, BDy + (int64_t)(r + ell) * ld, ld,
                     st));
+    }
+    // the new pairs are made biorthogonal to the earlier ones (X0 and the
+    // pairs locked before), twice: over the ~100 iterations between two
+    // locks the window drifts from the locked pairs by rounding (1.5e-9 in
+    // X^T Y at n = 32768 without this), since only W, Z are projected each
+    // iteration (eq. update_W/Z); the change is of that size and leaves the
+    // residuals below tol (they are recomputed with fresh products at the end)
+    const int prev = r + ell;
+    if (prev > 0) {
+      double* Xn = Dx + (int64_t)prev * ld;
+      double* Yn = Dy + (int64_t)prev * ld;
+      for (int c0 = 0; c0 < count; c0 += cgcols) {
+        const int cc = std::min(cgcols, count - c0);
+        const int64_t o = (int64_t)c0 * ld;
+        for (int pass = 0; pass < 2; ++pass) {
+          LST(gram(seg1(bdy(), ld, prev), seg1(Xn + o, ld, cc), Cproj, prev));
+          LST(update(cc, 1.0, seg1(Dx, ld, prev), Cproj, prev, -1.0, Xn + o));
+          if (gen) LST(update(cc, 1.0, seg1(BDx, ld, prev), Cproj, prev, -1.0, BDx + prev * ld + o));
+          LST(gram(seg1(bdx(), ld, prev), seg1(Yn + o, ld, cc), Cproj, prev));
+          LST(update(cc, 1.0, seg1(Dy, ld, prev), Cproj, prev, -1.0, Yn + o));
+          if (gen) LST(update(cc, 1.0, seg1(BDy, ld, prev), Cproj, prev, -1.0, BDy + prev * ld + o));
+        }
+      }
     }
     for (int i = 0; i < count; ++i) locked.push_back(h->lam[first + i]);
     ell += count;

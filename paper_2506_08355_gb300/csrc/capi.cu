@@ -440,8 +440,9 @@ lrep_status lrep_set_options(lrep_problem p, const lrep_options* o) {
       o->precision < LREP_PREC_FP64 || o->precision > LREP_PREC_MIXED_SLICED)
     return p->fail(LREP_ERR_ARG, "lrep_set_options: invalid value");
   if ((o->precision & LREP_PREC_MIXED_BF16X3) && p->op.kind != OP_DENSE &&
-      p->op.kind != OP_SPECTRAL)
-    return p->fail(LREP_ERR_ARG, "mixed-precision CG products need a dense or spectral operator");
+      p->op.kind != OP_SPECTRAL && p->op.kind != OP_STENCIL)
+    return p->fail(LREP_ERR_ARG,
+                   "mixed-precision CG products need a dense, stencil or spectral operator");
   const bool rebuild = (o->precision != p->opts.precision);
   p->opts = *o;
   if (rebuild) {

@@ -22,14 +22,20 @@ namespace {
 // marches along z over a chunk of planes; the z-1 / z+1 neighbours stay in
 // registers and the current plane (with a one-point halo) is staged in
 // shared memory, so each value is read from memory about once.
+// T is the arithmetic type: double for float64 products, float for the
+// inexact CG products of eq. block_GS under the mixed precision (loads and
+// stores stay float64; GB300 issues ~64x more FP32 than FP64 FMAs per SM,
+// so the float kernel is bound by memory instead of the FP64 pipe).
 constexpr int STX = 32, STY = 8;
 
+template <typename T>
 __global__ void __launch_bounds__(STX * STY)
-stencil_kernel(int nx, int ny, int nz, double coef, const double* __restrict__ d,
+stencil_kernel(int nx, int ny, int nz, double coef_d, const double* __restrict__ d,
                const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
                int64_t ldy, int zchunk, int tiles_x, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  __shared__ double s[STY + 2][STX + 2];
+  const T coef = (T)coef_d;
+  __shared__ T s[STY + 2][STX + 2];
   const int tx = threadIdx.x % STX, ty = threadIdx.x / STX;
   const int tile = blockIdx.x;
   const int i0 = (tile % tiles_x) * STX, j0 = (tile / tiles_x) * STY;
@@ -41,25 +47,27 @@ stencil_kernel(int nx, int ny, int nz, double coef, const double* __restrict__ d
   const double* x = X + (int64_t)blockIdx.z * ldx;
   double* y = Y + (int64_t)blockIdx.z * ldy;
   const int64_t p0 = (int64_t)j * nx + i;
-  double below = (in && z0 > 0) ? x[p0 + (int64_t)(z0 - 1) * plane] : 0.0;
-  double cur = (in && z0 < nz) ? x[p0 + (int64_t)z0 * plane] : 0.0;
+  T below = (in && z0 > 0) ? (T)x[p0 + (int64_t)(z0 - 1) * plane] : (T)0;
+  T cur = (in && z0 < nz) ? (T)x[p0 + (int64_t)z0 * plane] : (T)0;
   for (int z = z0; z < z1; ++z) {
     const int64_t pz = (int64_t)z * plane;
-    const double above = (in && z + 1 < nz) ? x[p0 + pz + plane] : 0.0;
+    const T above = (in && z + 1 < nz) ? (T)x[p0 + pz + plane] : (T)0;
     s[ty + 1][tx + 1] = cur;
     // halo: left/right columns by the first/last lane of each row, top/
     // bottom rows by the first/last warp
-    if (tx == 0) s[ty + 1][0] = (i0 > 0 && j < ny) ? x[pz + (int64_t)j * nx + i0 - 1] : 0.0;
+    if (tx == 0) s[ty + 1][0] = (i0 > 0 && j < ny) ? (T)x[pz + (int64_t)j * nx + i0 - 1] : (T)0;
     if (tx == STX - 1)
-      s[ty + 1][STX + 1] = (i0 + STX < nx && j < ny) ? x[pz + (int64_t)j * nx + i0 + STX] : 0.0;
-    if (ty == 0) s[0][tx + 1] = (j0 > 0 && i < nx) ? x[pz + (int64_t)(j0 - 1) * nx + i] : 0.0;
+      s[ty + 1][STX + 1] =
+          (i0 + STX < nx && j < ny) ? (T)x[pz + (int64_t)j * nx + i0 + STX] : (T)0;
+    if (ty == 0) s[0][tx + 1] = (j0 > 0 && i < nx) ? (T)x[pz + (int64_t)(j0 - 1) * nx + i] : (T)0;
     if (ty == STY - 1)
-      s[STY + 1][tx + 1] = (j0 + STY < ny && i < nx) ? x[pz + (int64_t)(j0 + STY) * nx + i] : 0.0;
+      s[STY + 1][tx + 1] =
+          (j0 + STY < ny && i < nx) ? (T)x[pz + (int64_t)(j0 + STY) * nx + i] : (T)0;
     __syncthreads();
     if (in) {
-      const double lap = s[ty + 1][tx] + s[ty + 1][tx + 2] + s[ty][tx + 1] + s[ty + 2][tx + 1] +
-                         below + above - 6.0 * cur;
-      y[p0 + pz] = fma(coef, lap, d[p0 + pz] * cur);
+      const T lap = s[ty + 1][tx] + s[ty + 1][tx + 2] + s[ty][tx + 1] + s[ty + 2][tx + 1] +
+                    below + above - (T)6 * cur;
+      y[p0 + pz] = (double)fma(coef, lap, (T)d[p0 + pz] * cur);
     }
     __syncthreads();
     below = cur;
@@ -221,6 +229,12 @@ cudaError_t stencil_apply_f64(int nx, int ny, int nz, double coef_h2,
                               const double* d, int c, const double* X,
                               int64_t ldx, double* Y, int64_t ldy,
                               const int* skip, cudaStream_t st) {
+  return stencil_apply(false, nx, ny, nz, coef_h2, d, c, X, ldx, Y, ldy, skip, st);
+}
+
+cudaError_t stencil_apply(bool f32, int nx, int ny, int nz, double coef_h2, const double* d,
+                          int c, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                          const int* skip, cudaStream_t st) {
   if (c <= 0) return cudaSuccess;
   const int tiles_x = (nx + STX - 1) / STX, tiles_y = (ny + STY - 1) / STY;
   const int tiles = tiles_x * tiles_y;
@@ -229,8 +243,13 @@ cudaError_t stencil_apply_f64(int nx, int ny, int nz, double coef_h2,
   zchunks = std::min(zchunks, std::max(1, nz / 8));
   const int zchunk = (nz + zchunks - 1) / zchunks;
   zchunks = (nz + zchunk - 1) / zchunk;
-  stencil_kernel<<<dim3(tiles, zchunks, c), STX * STY, 0, st>>>(
-      nx, ny, nz, coef_h2, d, X, ldx, Y, ldy, zchunk, tiles_x, skip); LREP_COUNT_LAUNCH();
+  if (f32)
+    stencil_kernel<float><<<dim3(tiles, zchunks, c), STX * STY, 0, st>>>(
+        nx, ny, nz, coef_h2, d, X, ldx, Y, ldy, zchunk, tiles_x, skip);
+  else
+    stencil_kernel<double><<<dim3(tiles, zchunks, c), STX * STY, 0, st>>>(
+        nx, ny, nz, coef_h2, d, X, ldx, Y, ldy, zchunk, tiles_x, skip);
+  LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

@@ -22,6 +22,11 @@ cudaError_t stencil_apply_f64(int nx, int ny, int nz, double coef_h2,
                               const double* d, int c, const double* X,
                               int64_t ldx, double* Y, int64_t ldy,
                               const int* skip, cudaStream_t st);
+// the same product with float64 (f32 = false) or float32 arithmetic (f32 =
+// true: the inexact CG products under the mixed precision)
+cudaError_t stencil_apply(bool f32, int nx, int ny, int nz, double coef_h2, const double* d,
+                          int c, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                          const int* skip, cudaStream_t st);
 
 // Fourier spectral operator on a periodic grid (k_spectral.cu):
 // Y = coef * Lap_F X + d .* X, with scale[ax] = -coef * (2 pi / L_ax)^2 / N_ax

@@ -1,8 +1,9 @@
 // Tensor-core operators of the dense K and M, built once per problem from
 // the float64 matrices according to opts.precision:
 //  * bit 0 (MIXED_BF16X3): hi + lo bfloat16 split for the inexact CG
-//    products of eq. block_GS (k_tc.cu); spectral operators need no split
-//    and run those products with float32 transforms (k_spectral.cu);
+//    products of eq. block_GS (k_tc.cu); spectral and stencil operators need
+//    no split and run those products with float32 arithmetic (k_spectral.cu,
+//    k_ops.cu);
 //  * bit 1 (FP64_SLICED): seven bf16 digit planes for float64-accurate
 //    products by error-free slicing (k_oz.cu): every product that enters H^
 //    (eq. hat_H) and every residual (eq. tol), and the CG products when bit 0
@@ -26,7 +27,7 @@ bool split_ready(lrep_problem p) {
   const Operator& o = p->op;
   const bool dense = o.kind == OP_DENSE;
   return (p->opts.precision == LREP_PREC_FP64 || o.tc_err) &&
-         (!want_tc(p) || o.tcK || o.kind == OP_SPECTRAL) &&
+         (!want_tc(p) || o.tcK || o.kind == OP_SPECTRAL || o.kind == OP_STENCIL) &&
          (!want_oz(p) || !dense || (o.ozK && (!o.hasB || o.ozB)));
 }
 
@@ -44,8 +45,9 @@ lrep_status build_split(lrep_problem p) {
   Operator& o = p->op;
   free_split(p);
   if (p->opts.precision == LREP_PREC_FP64) return LREP_OK;
-  if (want_tc(p) && o.kind != OP_DENSE && o.kind != OP_SPECTRAL)
-    return p->fail(LREP_ERR_ARG, "mixed-precision CG products need a dense or spectral operator");
+  if (want_tc(p) && o.kind != OP_DENSE && o.kind != OP_SPECTRAL && o.kind != OP_STENCIL)
+    return p->fail(LREP_ERR_ARG,
+                   "mixed-precision CG products need a dense, stencil or spectral operator");
   const int64_t n = o.n;
   const double* src[2] = {o.K, o.M};
   if (want_tc(p) && o.kind == OP_DENSE) {
@@ -145,6 +147,14 @@ lrep_status apply_op_cg(lrep_problem p, int which, int c, const double* X,
                         double* ws, size_t ws_elems) {
   if (!want_tc(p)) return apply_op(p, which, c, X, ldx, Y, ldy, skip, ws, ws_elems);
   const Operator& o = p->op;
+  if (o.kind == OP_STENCIL) {  // float32 arithmetic, float64 loads and stores
+    const cudaError_t e = stencil_apply(true, o.nx, o.ny, o.nz, o.coef_h2,
+                                        which == LREP_OP_K ? o.dK : o.dM, c, X, ldx, Y, ldy,
+                                        skip, p->stream);
+    if (e != cudaSuccess)
+      return p->fail(LREP_ERR_CUDA, std::string("stencil product: ") + cudaGetErrorString(e));
+    return LREP_OK;
+  }
   if (o.kind == OP_SPECTRAL) {  // float32 transforms
     const int dims[3] = {o.nx, o.ny, o.nz};
     const cudaError_t e = spectral_apply(true, dims, o.spec_scale,

@@ -1,10 +1,14 @@
 // Serving loop of lrep.h: continuous batching of concurrent BOSP solves.
 //
-//  * Admission: requests wait in arrival order; the head is admitted when a
-//    slot is free and its device footprint (the solver workspace, plus the
-//    bf16 operator split in mixed mode) fits the HBM budget next to the
-//    solves already running.  Slots free up as solves finish, so requests
-//    that arrive while others run are admitted as soon as they fit.
+//  * Admission: when a slot is free, the queued request with the smallest
+//    device footprint (the solver workspace, plus the bf16 operator split
+//    in mixed mode) that fits the HBM budget next to the solves already
+//    running starts; a request that has been passed over kMaxOvertakes
+//    times goes first once it fits (nothing starves), and while it does not
+//    fit nothing overtakes it.  Slots free up as solves finish, so requests
+//    that arrive while others run are admitted as soon as they fit, and a
+//    large request waiting for memory does not hold up small ones behind
+//    it.
 //  * Overlap: every slot is a host thread with its own CUDA stream; the
 //    solve of an admitted request runs on its slot's stream, so the work of
 //    concurrent requests overlaps on the device.
@@ -33,6 +37,7 @@ using namespace lrep;
 namespace {
 
 constexpr int kMaxBatch = 16;
+constexpr int kMaxOvertakes = 64;  // admissions a queued request lets pass
 
 // Rendezvous of the small LREPs of concurrently running solves.
 struct Batcher : SmallBatcher {
@@ -136,6 +141,7 @@ struct Req {
   int nev, block;
   double tol;
   size_t footprint;
+  int overtaken = 0;  // later arrivals admitted before this one
 };
 
 }  // namespace
@@ -155,11 +161,22 @@ struct lrep_server_s {
   std::vector<std::thread> workers;
   Batcher batcher;
 
-  // next request that may start now (arrival order, no overtaking)
-  bool admissible() const {
-    return !queue.empty() && idle > 0 &&
-           (int64_t)queue.front().footprint + in_use <= budget;
+  bool fits(const Req& r) const { return (int64_t)r.footprint + in_use <= budget; }
+
+  // index in the queue of the request to start now, or -1: the oldest
+  // request passed over kMaxOvertakes times if any (when it fits), else the
+  // smallest footprint that fits (ties: arrival order)
+  int pick() const {
+    if (queue.empty() || idle <= 0) return -1;
+    for (size_t i = 0; i < queue.size(); ++i)
+      if (queue[i].overtaken >= kMaxOvertakes) return fits(queue[i]) ? (int)i : -1;
+    int best = -1;
+    for (size_t i = 0; i < queue.size(); ++i)
+      if (fits(queue[i]) && (best < 0 || queue[i].footprint < queue[best].footprint))
+        best = (int)i;
+    return best;
   }
+  bool admissible() const { return pick() >= 0; }
 
   void worker() {
     cudaSetDevice(device);
@@ -173,12 +190,13 @@ struct lrep_server_s {
         cv_work.notify_all();
         cv_work.wait(g, [&] { return stop || admissible(); });
         // decide while this worker still counts as idle
-        const bool take = admissible();
+        const int k = pick();
         idle--;
         if (stop && queue.empty()) break;
-        if (!take) continue;
-        r = queue.front();
-        queue.pop_front();
+        if (k < 0) continue;
+        r = queue[k];
+        for (int i = 0; i < k; ++i) queue[i].overtaken++;
+        queue.erase(queue.begin() + k);
         in_use += (int64_t)r.footprint;
         std::lock_guard<std::mutex> bg(batcher.mu);
         batcher.running++;

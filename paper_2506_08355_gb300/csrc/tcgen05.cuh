@@ -73,15 +73,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// L2 prefetch of one 2-D TMA box (no shared memory, no completion): moves
-// a later tile's HBM traffic ahead of its load into shared memory
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                   (uint64_t)map),
-               "r"(x), "r"(y)
-               : "memory");
-}
-
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (SBO), descriptor version 1
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -91,20 +82,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   d |= (uint64_t)(1024 >> 4) << 32;     // SBO
   d |= (uint64_t)1 << 46;               // version
   d |= (uint64_t)2 << 61;               // SWIZZLE_128B
-  return d;
-}
-
-// shared-memory matrix descriptor of an MN-major operand with 128-byte
-// swizzle: the tile holds K rows of 128 bytes (64 consecutive M/N values
-// each), 8-row swizzle atoms 1024 bytes apart along K (SBO) and 64-value
-// atoms `lbo` bytes apart along M/N (LBO), descriptor version 1
-__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;  // LBO: stride between M/N atoms
-  d |= (uint64_t)(1024 >> 4) << 32;             // SBO: stride between 8-row K groups
-  d |= (uint64_t)1 << 46;                       // version
-  d |= (uint64_t)2 << 61;                       // SWIZZLE_128B
   return d;
 }
 
@@ -120,14 +97,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b,
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-// same, always accumulating into D
-__device__ __forceinline__ void mma_bf16_acc(uint32_t dtmem, uint64_t a, uint64_t b,
-                                             uint32_t idesc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.eq.u32 p, 1, 1;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(idesc));
 }
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(

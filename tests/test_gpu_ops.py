@@ -227,12 +227,8 @@ def test_bf16x3_tensor_core_product(L, n, c):
     """Mixed-precision CG product (tcgen05, bf16 hi/lo split, fp32
     accumulation) against the float64 product.  Error model: dropping the
     lo*lo term and rounding lo leave ~2^-16 relative per operand, fp32
-    accumulation adds ~k 2^-24; bound 1e-4 of |A||X| with margin.
-    Up to 32 columns the symmetric kernel runs (upper tiles only, each
-    off-diagonal tile used as A_IJ and A_IJ^T): n = 200 and 1000 have one
-    tile per super-block, n = 8192 (c = 16) super-blocks of 2 x 2 tiles and
-    n = 12000 of 3 x 3 tiles with a ragged last super-row and tile; c = 37
-    and 64 take the split-K kernel."""
+    accumulation adds ~k 2^-24; bound 1e-4 of |A||X| with margin.  Shapes
+    with ragged row tiles, k-tiles and column counts (N padded to 16)."""
     rng = np.random.default_rng(n + c)
     A = rng.standard_normal((n, n))
     K = (A + A.T) * 0.5
@@ -285,3 +281,32 @@ def test_cg_matches_oracle_columnwise(L, prec_name):
             assert err.max() < 1e-11, (op, tol, maxit, err.max())
             assert np.all(X[:, 5] == 0.0)
     prob.close()
+
+
+
+@pytest.mark.parametrize("dims", [(17, 9, 5), (64, 64, 64)])
+def test_stencil_float32_cg_product(L, dims):
+    """The stencil's CG product under the mixed precision (float32 sums,
+    float64 loads and stores) against the float64 product: error bounded by
+    ~2^-23 of |coef| |Lap| |X| + |d| |X| (bound 1e-6 of that scale), and
+    visibly not the float64 path."""
+    nx, ny, nz = dims
+    s = synth.bdg_stencil(nx, ny, nz)
+    n = s["n"]
+    rng = np.random.default_rng(nx)
+    X = rng.standard_normal((n, 5))
+    p = L.Problem.stencil(nx, ny, nz, s["h"], -0.5, s["dK"], s["dM"])
+    p.set_options(precision=L.PREC_MIXED_BF16X3)
+    op = R.StencilOp(nx, ny, nz, s["h"], -0.5, s["dK"], s["dM"])
+    absop = R.StencilOp(nx, ny, nz, s["h"], 0.5, np.abs(s["dK"]) + 6.0 / s["h"] ** 2,
+                        np.abs(s["dM"]) + 6.0 / s["h"] ** 2)
+    Y = L.device_block(n, 5)
+    for which, name in ((L.OP_K, "K"), (L.OP_M, "M")):
+        p.apply(which, to_dev(X), Y, cg=True)
+        got = from_dev(Y)
+        ref = op.apply(name, X)
+        scale = absop.apply(name, np.abs(X))
+        err = (np.abs(got - ref) / scale).max()
+        assert err < 1e-6, err
+        assert err > 1e-12
+    p.close()

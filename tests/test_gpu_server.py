@@ -97,3 +97,49 @@ def test_request_larger_than_budget_rejected(L):
         srv.submit(prob, 8, 8, 1e-8)
     srv.close()
     prob.close()
+
+
+def test_small_requests_overtake_one_waiting_for_memory(L):
+    """Admission by footprint: a large request that does not fit next to a
+    running one waits, and smaller requests behind it that fit start
+    meanwhile (no head-of-line blocking).  The mix includes projected
+    problems of order >= 40 (nev 16 and 24: grid-wide small LREP) and
+    batched ones; every result equals its solo solve to the last bit."""
+    reqs = [(1500, 16, 16, 0, 51),   # running first (order 48)
+            (2600, 24, 24, 0, 52),   # large: waits for memory
+            (400, 4, 4, 0, 53),      # small: fits next to the first
+            (500, 8, 8, 1, 54)]      # small
+    alone = []
+    for (n, nev, nb, prec, seed) in reqs:
+        p, prob = _make(L, n, prec, seed)
+        assert prob.solve(nev, nb, 1e-8) == L.OK
+        alone.append((prob.eigvals(), prob.vectors()))
+        prob.close()
+    made = [_make(L, n, prec, seed) for (n, nev, nb, prec, seed) in reqs]
+    fps = [prob.footprint(nev, nb) for (p, prob), (n, nev, nb, _, _) in zip(made, reqs)]
+    # room for the first and the two small ones together, or for the large
+    # one alone, never for the first and the large one together
+    budget = max(fps[0] + fps[2] + fps[3], fps[1]) + 1
+    assert fps[0] + fps[1] > budget
+    srv = L.Server(hbm_budget_bytes=budget, max_slots=3)
+    import time
+    t0 = time.perf_counter()
+    tickets = [srv.submit(prob, nev, nb, 1e-8)
+               for (p, prob), (n, nev, nb, _, _) in zip(made, reqs)]
+    done = {}
+    while len(done) < len(tickets):
+        for k, t in enumerate(tickets):
+            if k in done:
+                continue
+            st = srv.wait(t, 0)
+            if st != -6:
+                assert st == L.OK, (k, st)
+                done[k] = time.perf_counter() - t0
+        time.sleep(0.001)
+    # the small requests finished before the large one started and ended
+    assert done[2] < done[1] and done[3] < done[1], done
+    for (p, prob), (lam0, X0) in zip(made, alone):
+        np.testing.assert_allclose(prob.eigvals(), lam0, rtol=1e-14, atol=0)
+        np.testing.assert_allclose(prob.vectors(), X0, rtol=0, atol=1e-14)
+        prob.close()
+    srv.close()

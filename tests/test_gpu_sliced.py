@@ -221,18 +221,21 @@ def test_sliced_update_error_bound(L, n, k, c):
     assert worst <= 1.0, worst
 
 
-def test_sliced_tall_skinny_full_size_stencil(L):
-    """The 64^3 BdG-like stencil workload with precision FP64_SLICED: the
+@pytest.mark.parametrize("prec_name", ["PREC_FP64_SLICED", "PREC_MIXED_SLICED"])
+def test_sliced_tall_skinny_full_size_stencil(L, prec_name):
+    """The 64^3 BdG-like stencil workload with precision FP64_SLICED (the
     stencil products stay FP64, the Grams and block updates run sliced on the
-    tensor cores; same eigenvalues as the oracle's stored literal Alg. 2 run,
-    residuals and biorthogonality re-checked on the CPU."""
+    tensor cores) and MIXED_SLICED (the CG products of eq. block_GS in
+    float32 arithmetic as well); same eigenvalues as the oracle's stored
+    literal Alg. 2 run, residuals and biorthogonality re-checked on the
+    CPU."""
     from test_gpu_solver import _stored_run
     lam_ref, _ = _stored_run("config2_oracle_run.txt")
     p = synth.config(2)
     op = R.StencilOp(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"], p["dM"])
     prob = L.Problem.stencil(p["nx"], p["ny"], p["nz"], p["h"], -0.5, p["dK"], p["dM"])
     prob.set_nullspace(p["X0"])
-    prob.set_options(precision=L.PREC_FP64_SLICED)
+    prob.set_options(precision=getattr(L, prec_name))
     assert prob.solve(32, 16, 1e-10) == L.OK
     lam, X, Y = check(op, prob, lam_ref, 1e-10, 32, rtol=1e-10)
     assert np.abs(p["X0"][:, 0] @ Y).max() < 1e-9
