@@ -22,10 +22,6 @@ namespace {
 // marches along z over a chunk of planes; the z-1 / z+1 neighbours stay in
 // registers and the current plane (with a one-point halo) is staged in
 // shared memory, so each value is read from memory about once.
-// T is the arithmetic type: double for float64 products, float for the
-// inexact CG products of eq. block_GS under the mixed precision (loads and
-// stores stay float64; GB300 issues ~64x more FP32 than FP64 FMAs per SM,
-// so the float kernel is bound by memory instead of the FP64 pipe).
 constexpr int STX = 32, STY = 8;
 
 template <typename T>
@@ -72,6 +68,64 @@ stencil_kernel(int nx, int ny, int nz, double coef_d, const double* __restrict__
     __syncthreads();
     below = cur;
     cur = above;
+  }
+}
+
+// z-marching form for the float32 CG products: the 32 x 8 tile of the
+// 2.5-D form, four columns per thread, but no shared memory and no
+// barriers: the x and y neighbours are the tile's own loads of the same
+// plane (L1 hits), the z neighbours stay in registers, and the warps march
+// independently with the next planes' loads in flight.  The float64
+// products stay on the 2.5-D form, which is bound by the FP64 pipe on
+// GB300 (~8 FP64 operations per point and column) either way.
+constexpr int SZC = 4;  // columns per thread
+
+__global__ void __launch_bounds__(STX * STY)
+stencil_z_f32_kernel(int nx, int ny, int nz, float coef, const double* __restrict__ d,
+                     int c, const double* __restrict__ X, int64_t ldx,
+                     double* __restrict__ Y, int64_t ldy, int zchunk, int tiles_x,
+                     const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int tx = threadIdx.x % STX, ty = threadIdx.x / STX;
+  const int tile = blockIdx.x;
+  const int i = (tile % tiles_x) * STX + tx, j = (tile / tiles_x) * STY + ty;
+  if (i >= nx || j >= ny) return;
+  const int z0 = blockIdx.y * zchunk, z1 = min(nz, z0 + zchunk);
+  const int c0 = blockIdx.z * SZC;
+  const int64_t plane = (int64_t)nx * ny;
+  const bool xl = i > 0, xr = i + 1 < nx, yl = j > 0, yr = j + 1 < ny;
+  const double* x[SZC];
+  double* y[SZC];
+  float below[SZC], cur[SZC];
+  const int64_t p0 = (int64_t)j * nx + i + (int64_t)z0 * plane;
+#pragma unroll
+  for (int q = 0; q < SZC; ++q) {
+    const int col = min(c0 + q, c - 1);
+    x[q] = X + (int64_t)col * ldx + p0;
+    y[q] = Y + (int64_t)col * ldy + p0;
+    below[q] = z0 > 0 ? (float)__ldg(x[q] - plane) : 0.f;
+    cur[q] = (float)__ldg(x[q]);
+  }
+  const double* dz = d + p0;
+  const int ncol = min(SZC, c - c0);
+#pragma unroll 2
+  for (int z = z0; z < z1; ++z) {
+    const bool up = z + 1 < nz;
+    const float dp = (float)__ldg(dz);
+#pragma unroll
+    for (int q = 0; q < SZC; ++q) {
+      const double* xq = x[q];
+      const float above = up ? (float)__ldg(xq + plane) : 0.f;
+      const float s4 = (xl ? (float)__ldg(xq - 1) : 0.f) + (xr ? (float)__ldg(xq + 1) : 0.f) +
+                       (yl ? (float)__ldg(xq - nx) : 0.f) + (yr ? (float)__ldg(xq + nx) : 0.f);
+      const float lap = s4 + below[q] + above - 6.f * cur[q];
+      if (q < ncol) *y[q] = (double)fmaf(coef, lap, dp * cur[q]);
+      below[q] = cur[q];
+      cur[q] = above;
+      x[q] = xq + plane;
+      y[q] += plane;
+    }
+    dz += plane;
   }
 }
 
@@ -243,12 +297,19 @@ cudaError_t stencil_apply(bool f32, int nx, int ny, int nz, double coef_h2, cons
   zchunks = std::min(zchunks, std::max(1, nz / 8));
   const int zchunk = (nz + zchunks - 1) / zchunks;
   zchunks = (nz + zchunk - 1) / zchunk;
-  if (f32)
-    stencil_kernel<float><<<dim3(tiles, zchunks, c), STX * STY, 0, st>>>(
-        nx, ny, nz, coef_h2, d, X, ldx, Y, ldy, zchunk, tiles_x, skip);
-  else
+  if (f32) {
+    const int cgrp = (c + SZC - 1) / SZC;
+    int zc = (int)std::max<int64_t>(1, (4 * kNumSMs + (int64_t)tiles * cgrp - 1) /
+                                           ((int64_t)tiles * cgrp));
+    zc = std::min(zc, std::max(1, nz / 4));
+    const int zch = (nz + zc - 1) / zc;
+    zc = (nz + zch - 1) / zch;
+    stencil_z_f32_kernel<<<dim3(tiles, zc, cgrp), STX * STY, 0, st>>>(
+        nx, ny, nz, (float)coef_h2, d, c, X, ldx, Y, ldy, zch, tiles_x, skip);
+  } else {
     stencil_kernel<double><<<dim3(tiles, zchunks, c), STX * STY, 0, st>>>(
         nx, ny, nz, coef_h2, d, X, ldx, Y, ldy, zchunk, tiles_x, skip);
+  }
   LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }
