@@ -731,7 +731,9 @@ KERNELS = {  # the kernels behind each profiled class of solver work
     "gram": "gram_kernel / sliced Gram (oz_colslice + oz_gemm + oz_reduce)",
     "update": "update_kernel / sliced update (oz_rowslice + oz_gemm + oz_reduce)",
     "small": "small_front_kernel + FP64 refinement / small_lrep_one_kernel, small_pq",
-    "cg_vec": "cg_alpha + cg_update + cg_pdir",
+    "cg_vec": ("cg_alpha + cg_update + cg_pdir (dense mixed precision: cg_sum_alpha "
+               "+ cg_update + cg_pdir_split, the product's split-K sum and the "
+               "directions' bf16 split fused in)"),
     "alg1": "biorth_coef_kernel / biorth_lu_kernel",
     "other": "residual, right-hand-side and column-norm kernels",
 }
@@ -740,7 +742,7 @@ KERNELS = {  # the kernels behind each profiled class of solver work
 def product_kernel_names(config, prec, nb):
     import paper_2506_08355_gb300.lrep as lrep
     if config == 2:
-        cg = ("stencil_kernel<float> (2.5-D)" if prec & lrep.PREC_MIXED_BF16X3
+        cg = ("stencil_z_f32_kernel" if prec & lrep.PREC_MIXED_BF16X3
               else "stencil_kernel<double> (2.5-D)")
         return cg, "stencil_kernel<double> (2.5-D)"
     if config == 5:
@@ -750,7 +752,7 @@ def product_kernel_names(config, prec, nb):
     f64 = ("oz_gemm_kernel (+ X digit planes, split-K sum)" if prec & lrep.PREC_FP64_SLICED
            else "dense_apply_kernel (+ split-K reduce)")
     if prec & lrep.PREC_MIXED_BF16X3:
-        cg = "bf16x3_kernel (+ X split, split-K sum)"
+        cg = "bf16x3_kernel (+ the X split of each CG solve's first step)"
     else:
         cg = f64
     return cg, f64

@@ -431,6 +431,15 @@ struct Solver {
   lrep_status apply(int which, int c, const double* X, double* Y,
                     const int* skip = nullptr, bool cgop = false) {
     if (c <= 0) return LREP_OK;
+    return product(c, skip, cgop, [&] {
+      return cgop ? apply_op_cg(p, which, c, X, ld, Y, ld, skip, ws, ws_elems)
+                  : apply_op(p, which, c, X, ld, Y, ld, skip, ws, ws_elems);
+    });
+  }
+  // one operator product `run` of c columns, counted and (when profiling)
+  // timed as its class
+  template <class F>
+  lrep_status product(int c, const int* skip, bool cgop, F&& run) {
     p->matvecs += skip ? 0 : c;
     const bool prof = p->opts.profile != 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -439,8 +448,7 @@ struct Solver {
       LST(take_event(&e1));
       LCK(cudaEventRecord(e0, st));
     }
-    lrep_status s = cgop ? apply_op_cg(p, which, c, X, ld, Y, ld, skip, ws, ws_elems)
-                         : apply_op(p, which, c, X, ld, Y, ld, skip, ws, ws_elems);
+    lrep_status s = run();
     if (prof && s == LREP_OK) {
       LCK(cudaEventRecord(e1, st));
       int flag = -1;
@@ -499,14 +507,31 @@ struct Solver {
       LCK(cg_init(n, c, B, ld, X, Rr, Pr, ld, ctol, cg, st));
       return LREP_OK;
     }));
+    // dense operator under the mixed precision: the product's split-K sum
+    // runs inside cg_sum_alpha and the directions' bf16 split inside
+    // cg_pdir_split (same arithmetic, two launches and passes fewer)
+    const bool fused = cgop && c > 0 && cg_fused(p);
     for (int it = 0; it < maxit; ++it) {
-      LST(apply(which, c, Pr, Qr, cg.done, cgop));
-      LST(timed(LREP_PC_CGVEC, [&] {
-        LCK(cg_alpha(n, c, Pr, Qr, ld, cg, st));
-        LCK(cg_update(n, c, X, Rr, Pr, Qr, ld, cg, st));
-        LCK(cg_pdir(n, c, Rr, Pr, ld, cg, st));
-        return LREP_OK;
-      }));
+      if (fused) {
+        CgFused fb{};
+        LST(product(c, cg.done, true, [&] {
+          return apply_cg_partials(p, which, c, Pr, ld, it > 0, cg.done, ws, ws_elems, &fb);
+        }));
+        LST(timed(LREP_PC_CGVEC, [&] {
+          LCK(cg_sum_alpha(n, c, fb.part, fb.splits, Pr, Qr, ld, cg, st));
+          LCK(cg_update(n, c, X, Rr, Pr, Qr, ld, cg, st));
+          LCK(cg_pdir_split(n, c, Rr, Pr, ld, cg, fb.xhi, fb.xlo, fb.ldb, st));
+          return LREP_OK;
+        }));
+      } else {
+        LST(apply(which, c, Pr, Qr, cg.done, cgop));
+        LST(timed(LREP_PC_CGVEC, [&] {
+          LCK(cg_alpha(n, c, Pr, Qr, ld, cg, st));
+          LCK(cg_update(n, c, X, Rr, Pr, Qr, ld, cg, st));
+          LCK(cg_pdir(n, c, Rr, Pr, ld, cg, st));
+          return LREP_OK;
+        }));
+      }
       if (check_every > 0 && (it + 1) % check_every == 0) {
         int done = 0;
         LCK(cudaMemcpyAsync(&h->cnt[3], cg.done, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -652,7 +652,18 @@ lrep_status lrep_op_cg(lrep_problem p, int32_t op, int32_t ncols, const double* 
   PCK(p, cudaMemsetAsync(cg.iters, 0, 8 * sizeof(int), p->stream));
   PCK(p, cudaMemsetAsync(cg.counter, 0, 8 * sizeof(unsigned int), p->stream));
   PCK(p, cg_init(n, ncols, B, ldb, X, R, P, ldx, tol, cg, p->stream));
+  const bool fused = cg_fused(p);  // as in the solver's CG
   for (int it = 0; it < maxit; ++it) {
+    if (fused) {
+      CgFused fb{};
+      const lrep_status s =
+          apply_cg_partials(p, op, ncols, P, ldx, it > 0, cg.done, ws, aws, &fb);
+      if (s != LREP_OK) return s;
+      PCK(p, cg_sum_alpha(n, ncols, fb.part, fb.splits, P, Q, ldx, cg, p->stream));
+      PCK(p, cg_update(n, ncols, X, R, P, Q, ldx, cg, p->stream));
+      PCK(p, cg_pdir_split(n, ncols, R, P, ldx, cg, fb.xhi, fb.xlo, fb.ldb, p->stream));
+      continue;
+    }
     const lrep_status s = apply_op_cg(p, op, ncols, P, ldx, Q, ldx, cg.done, ws, aws);
     if (s != LREP_OK) return s;
     PCK(p, cg_alpha(n, ncols, P, Q, ldx, cg, p->stream));

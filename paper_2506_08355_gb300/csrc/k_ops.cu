@@ -5,6 +5,7 @@
 // CG control stays on the device: each kernel reads the `done` flag and
 // returns at once when every column has converged, so the host can
 // enqueue the iteration budget without a read-back per step.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -273,6 +274,60 @@ __global__ void cg_pdir_kernel(int64_t n, const double* __restrict__ R,
   }
 }
 
+// cg_alpha_kernel with Q formed first from the split-K partials of the
+// tensor-core product (inactive columns: Q is not needed and not formed)
+__global__ void __launch_bounds__(256)
+cg_sum_alpha_kernel(int64_t n, int nb, const float* __restrict__ part, int splits,
+                    const double* __restrict__ P, double* __restrict__ Q, int64_t ld,
+                    CgState s, int64_t slab_rows) {
+  if (*s.done) return;
+  __shared__ double red[32];
+  const int col = blockIdx.y, slab = blockIdx.x, slabs = gridDim.x;
+  const int64_t r0 = (int64_t)slab * slab_rows, r1 = min(n, r0 + slab_rows);
+  double acc = 0.0;
+  if (s.active[col])
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      double q = 0.0;
+      for (int z = 0; z < splits; ++z) q += (double)part[((int64_t)z * nb + col) * n + i];
+      Q[i + (int64_t)col * ld] = q;
+      acc = fma(P[i + (int64_t)col * ld], q, acc);
+    }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) s.part[(int64_t)col * slabs + slab] = acc;
+  if (!arrive_last(s.counter)) return;
+  if (threadIdx.x == 0 && s.iters) *s.iters += 1;
+  for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+    double pq = 0.0;
+    for (int z = 0; z < slabs; ++z) pq += ld_cg(s.part + (int64_t)c * slabs + z);
+    if (s.active[c] && pq > 0.0 && isfinite(pq)) {
+      s.alpha[c] = s.rho[c] / pq;
+    } else {
+      s.alpha[c] = 0.0;
+      s.active[c] = 0;
+    }
+  }
+}
+
+// cg_pdir_kernel that also writes bf16 hi = bf16(p), lo = bf16(p - hi)
+__global__ void cg_pdir_split_kernel(int64_t n, const double* __restrict__ R,
+                                     double* __restrict__ P, int64_t ld, CgState s,
+                                     __nv_bfloat16* __restrict__ hi,
+                                     __nv_bfloat16* __restrict__ lo, int64_t ldb) {
+  if (*s.done) return;
+  const int col = blockIdx.y;
+  if (!s.active[col]) return;
+  const double b = s.beta[col];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = i + (int64_t)col * ld;
+    const double pv = fma(b, P[o], R[o]);
+    P[o] = pv;
+    const __nv_bfloat16 h = __double2bfloat16(pv);
+    hi[i + (int64_t)col * ldb] = h;
+    lo[i + (int64_t)col * ldb] = __double2bfloat16(pv - (double)__bfloat162float(h));
+  }
+}
+
 int cg_slabs(int64_t n) { return reduction_slabs(n, 2048, 64); }
 unsigned grid_rows(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2 * kNumSMs));
@@ -354,6 +409,22 @@ cudaError_t cg_update(int64_t n, int nb, double* X, double* R, const double* P,
 cudaError_t cg_pdir(int64_t n, int nb, const double* R, double* P, int64_t ld,
                     CgState& s, cudaStream_t st) {
   cg_pdir_kernel<<<dim3(grid_rows(n), nb), 256, 0, st>>>(n, R, P, ld, s); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t cg_sum_alpha(int64_t n, int nb, const float* part, int splits, const double* P,
+                         double* Q, int64_t ld, CgState& s, cudaStream_t st) {
+  const int64_t sr = (n + s.slabs - 1) / s.slabs;
+  cg_sum_alpha_kernel<<<dim3(s.slabs, nb), 256, 0, st>>>(n, nb, part, splits, P, Q, ld, s, sr);
+  LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t cg_pdir_split(int64_t n, int nb, const double* R, double* P, int64_t ld,
+                          CgState& s, void* hi, void* lo, int64_t ldb, cudaStream_t st) {
+  cg_pdir_split_kernel<<<dim3(grid_rows(n), nb), 256, 0, st>>>(
+      n, R, P, ld, s, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, ldb);
+  LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

@@ -164,32 +164,41 @@ bf16x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ 
                  "r"(tmem_cols));
 }
 
+// hi = bf16(a), lo = bf16(a - hi); columns over grid y, rows over grid x
 __global__ void split_bf16_kernel(int64_t rows, int64_t cols, const double* __restrict__ A,
                                   int64_t lda, __nv_bfloat16* __restrict__ hi,
                                   __nv_bfloat16* __restrict__ lo, int64_t ldb) {
-  const int64_t tot = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;
-    const double a = A[i + j * lda];
-    const __nv_bfloat16 h = __double2bfloat16(a);
-    hi[i + j * ldb] = h;
-    lo[i + j * ldb] = __double2bfloat16(a - (double)__bfloat162float(h));
-  }
+  for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const double a = A[i + j * lda];
+      const __nv_bfloat16 h = __double2bfloat16(a);
+      hi[i + j * ldb] = h;
+      lo[i + j * ldb] = __double2bfloat16(a - (double)__bfloat162float(h));
+    }
 }
 
+// Y = sum over the splits of the fp32 partials, in split order, in fp64;
+// column j = blockIdx.y
 __global__ void splitk_sum_kernel(int64_t n, int c, int splits, const float* __restrict__ part,
                                   double* __restrict__ Y, int64_t ldy,
                                   const int* __restrict__ skip) {
   if (skip && *skip) return;
-  const int64_t tot = n * c;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / n, i = e % n;
+  const int j = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int z = 0; z < splits; ++z) s += (double)part[((int64_t)z * c + j) * n + i];
     Y[i + j * ldy] = s;
   }
+}
+
+// 2-D launch shape of the column-wise kernels above: ~4 CTAs per SM in all
+dim3 colwise_grid(int64_t rows, int64_t cols) {
+  const int64_t gy = std::min<int64_t>(std::max<int64_t>(cols, 1), 65535);
+  const int64_t want = std::max<int64_t>(1, (4 * kNumSMs + gy - 1) / gy);
+  const int64_t gx = std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, want));
+  return dim3((unsigned)gx, (unsigned)gy);
 }
 
 // signature of cuTensorMapEncodeTiled (driver API, obtained at run time)
@@ -241,10 +250,9 @@ int64_t tc_ld(int64_t n) { return ((n + 63) / 64) * 64; }
 
 cudaError_t tc_split_matrix(int64_t rows, int64_t cols, const double* A, int64_t lda, void* hi,
                             void* lo, int64_t ldb, cudaStream_t st) {
-  const int64_t tot = rows * cols;
-  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 16 * kNumSMs));
-  split_bf16_kernel<<<g, 256, 0, st>>>(rows, cols, A, lda, (__nv_bfloat16*)hi,
-                                       (__nv_bfloat16*)lo, ldb); LREP_COUNT_LAUNCH();
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  split_bf16_kernel<<<colwise_grid(rows, cols), 256, 0, st>>>(
+      rows, cols, A, lda, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, ldb); LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -267,26 +275,34 @@ size_t tc_ws_bytes(int64_t n, int c) {
   return (size_t)2 * ldb * c * 2 + (size_t)tc_splits(n) * c * n * 4 + 4096;
 }
 
-cudaError_t tc_apply(const TcOperand& A, int64_t n, int c, const double* X, int64_t ldx,
-                     double* Y, int64_t ldy, void* ws, size_t ws_bytes, int* err,
-                     const int* skip, cudaStream_t st) {
+TcBuffers tc_buffers(void* ws, int64_t n, int c) {
+  TcBuffers b;
+  b.ldb = tc_ld(n);
+  b.xhi = ws;
+  b.xlo = (uint8_t*)ws + (size_t)b.ldb * c * 2;
+  b.part = (float*)(((uintptr_t)b.xlo + (size_t)b.ldb * c * 2 + 255) & ~(uintptr_t)255);
+  b.splits = tc_splits(n);
+  return b;
+}
+
+cudaError_t tc_product_partials(const TcOperand& A, int64_t n, int c, const double* X,
+                                int64_t ldx, bool x_split, void* ws, size_t ws_bytes, int* err,
+                                const int* skip, cudaStream_t st) {
   if (c <= 0) return cudaSuccess;
   if (c > 128) return cudaErrorInvalidValue;
   if (ws_bytes < tc_ws_bytes(n, c)) return cudaErrorInvalidValue;
-  const int64_t ldb = tc_ld(n);
-  uint8_t* w = (uint8_t*)ws;
-  __nv_bfloat16* xhi = (__nv_bfloat16*)w;
-  __nv_bfloat16* xlo = xhi + (size_t)ldb * c;
-  float* part = (float*)(((uintptr_t)(xlo + (size_t)ldb * c) + 255) & ~(uintptr_t)255);
-  cudaError_t e = tc_split_matrix(n, c, X, ldx, xhi, xlo, ldb, st);
-  if (e != cudaSuccess) return e;
+  const TcBuffers b = tc_buffers(ws, n, c);
+  if (!x_split) {
+    const cudaError_t e = tc_split_matrix(n, c, X, ldx, b.xhi, b.xlo, b.ldb, st);
+    if (e != cudaSuccess) return e;
+  }
   const int N = ((c + 15) / 16) * 16;
   CUtensorMap mxh, mxl;
-  if (!tc_make_map(&mxh, xhi, n, c, ldb, BK, N) || !tc_make_map(&mxl, xlo, n, c, ldb, BK, N))
+  if (!tc_make_map(&mxh, b.xhi, n, c, b.ldb, BK, N) ||
+      !tc_make_map(&mxl, b.xlo, n, c, b.ldb, BK, N))
     return cudaErrorInvalidValue;
   const int kt = (int)((n + BK - 1) / BK);
   const int per = tc_per(n);
-  const int s = (kt + per - 1) / per;
   int tcols = 32;
   while (tcols < N) tcols <<= 1;
   const int tile_x = N * BK * 2;
@@ -295,14 +311,21 @@ cudaError_t tc_apply(const TcOperand& A, int64_t n, int c, const double* X, int6
   static const cudaError_t attr = cudaFuncSetAttribute(
       bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (attr != cudaSuccess) return attr;
-  dim3 grid((unsigned)((n + BM - 1) / BM), (unsigned)s);
+  dim3 grid((unsigned)((n + BM - 1) / BM), (unsigned)b.splits);
   bf16x3_kernel<<<grid, 128, smem, st>>>(A.hi_map, A.lo_map, mxh, mxl, (int)n, c, N, per, kt,
-                                         tcols, part, err, skip); LREP_COUNT_LAUNCH();
-  e = cudaGetLastError();
+                                         tcols, b.part, err, skip); LREP_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t tc_apply(const TcOperand& A, int64_t n, int c, const double* X, int64_t ldx,
+                     double* Y, int64_t ldy, void* ws, size_t ws_bytes, int* err,
+                     const int* skip, cudaStream_t st) {
+  if (c <= 0) return cudaSuccess;
+  cudaError_t e = tc_product_partials(A, n, c, X, ldx, false, ws, ws_bytes, err, skip, st);
   if (e != cudaSuccess) return e;
-  const int64_t tot = n * c;
-  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 8 * kNumSMs));
-  splitk_sum_kernel<<<g, 256, 0, st>>>(n, c, s, part, Y, ldy, skip); LREP_COUNT_LAUNCH();
+  const TcBuffers b = tc_buffers(ws, n, c);
+  splitk_sum_kernel<<<colwise_grid(n, c), 256, 0, st>>>(n, c, b.splits, b.part, Y, ldy, skip);
+  LREP_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

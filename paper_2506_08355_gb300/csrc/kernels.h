@@ -130,6 +130,16 @@ cudaError_t cg_update(int64_t n, int nb, double* X, double* R, const double* P,
                       const double* Q, int64_t ld, CgState& s, cudaStream_t st);
 cudaError_t cg_pdir(int64_t n, int nb, const double* R, double* P, int64_t ld,
                     CgState& s, cudaStream_t st);
+// Fused steps of the CG on the bf16 hi/lo tensor-core operator:
+// cg_sum_alpha forms Q from the product's split-K partials (fp32,
+// part[(z * nb + j) * n + i], summed over z in order in fp64, as the
+// unfused product does) and then computes alpha as cg_alpha;
+// cg_pdir_split is cg_pdir that also writes the new directions' bf16
+// hi/lo split (the next product's operand, leading dimension ldb).
+cudaError_t cg_sum_alpha(int64_t n, int nb, const float* part, int splits, const double* P,
+                         double* Q, int64_t ld, CgState& s, cudaStream_t st);
+cudaError_t cg_pdir_split(int64_t n, int nb, const double* R, double* P, int64_t ld,
+                          CgState& s, void* hi, void* lo, int64_t ldb, cudaStream_t st);
 
 // ------------------------------------------------------------ small (1 CTA)
 // Small LREP of order d (batched: one CTA per problem).  Per problem:

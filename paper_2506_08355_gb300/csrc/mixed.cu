@@ -142,6 +142,25 @@ lrep_status apply_sliced(lrep_problem p, int which, int c, const double* X, int6
   return LREP_OK;
 }
 
+bool cg_fused(lrep_problem p) {
+  return want_tc(p) && p->op.kind == OP_DENSE && p->op.tcK && p->op.tcM;
+}
+
+lrep_status apply_cg_partials(lrep_problem p, int which, int c, const double* X, int64_t ldx,
+                              bool x_split, const int* skip, double* ws, size_t ws_elems,
+                              CgFused* out) {
+  const Operator& o = p->op;
+  if (!cg_fused(p)) return p->fail(LREP_ERR_STATE, "mixed precision operator split missing");
+  const cudaError_t e = tc_product_partials(which == LREP_OP_K ? *o.tcK : *o.tcM, o.n, c, X,
+                                            ldx, x_split, ws, ws_elems * sizeof(double),
+                                            o.tc_err, skip, p->stream);
+  if (e != cudaSuccess)
+    return p->fail(LREP_ERR_CUDA, std::string("tensor-core product: ") + cudaGetErrorString(e));
+  const TcBuffers b = tc_buffers(ws, o.n, c);
+  *out = CgFused{b.part, b.splits, b.xhi, b.xlo, b.ldb};
+  return LREP_OK;
+}
+
 lrep_status apply_op_cg(lrep_problem p, int which, int c, const double* X,
                         int64_t ldx, double* Y, int64_t ldy, const int* skip,
                         double* ws, size_t ws_elems) {

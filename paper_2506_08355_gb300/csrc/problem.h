@@ -133,6 +133,21 @@ lrep_status apply_op(lrep_problem p, int which, int c, const double* X,
 lrep_status apply_op_cg(lrep_problem p, int which, int c, const double* X,
                         int64_t ldx, double* Y, int64_t ldy, const int* skip,
                         double* ws, size_t ws_elems);
+// The CG product on the dense operator under the mixed precision in fused
+// form (cg_fused): the tensor-core product leaves its split-K partials for
+// cg_sum_alpha, and X's bf16 split may already be in place (written by
+// cg_pdir_split); out receives where both live in ws.
+struct CgFused {
+  const float* part;
+  int splits;
+  void* xhi;
+  void* xlo;
+  int64_t ldb;
+};
+bool cg_fused(lrep_problem p);
+lrep_status apply_cg_partials(lrep_problem p, int which, int c, const double* X, int64_t ldx,
+                              bool x_split, const int* skip, double* ws, size_t ws_elems,
+                              CgFused* out);
 // y = op(X) by the sliced float64 emulation (dense, digit planes built)
 lrep_status apply_sliced(lrep_problem p, int which, int c, const double* X,
                          int64_t ldx, double* Y, int64_t ldy, const int* skip,
