@@ -93,7 +93,7 @@ def parse():
                     help="skip the profiled run behind the roofline entry")
     ap.add_argument("--op", default=None, choices=["dense", "tc", "sliced", "small", "stencil",
                                                   "stencil32", "spectral", "spectral32", "gram",
-                                                  "nullspace"],
+                                                  "nullspace", "cg"],
                     help="time one hot-path step alone (for ncu captures) instead of solves")
     ap.add_argument("--n", type=int, default=8192, help="order for --op")
     ap.add_argument("--cols", type=int, default=16, help="block columns for --op")
@@ -457,6 +457,37 @@ def op_mode(args):
         per = {"tc": 4.0, "sliced": 14.0, "dense": 8.0}[args.op]
         work = {"flops": 2.0 * n * n * c * mult, "fp64_flops": 2.0 * n * n * c,
                 "bytes": per * n * n + 16.0 * n * c, "max_rel_err": err}
+        p.close()
+    elif args.op == "cg":
+        # the block CG of eq. block_GS under the mixed precision on an SPD
+        # operator (lrep_op_cg, tolerance 0: every step runs), against the
+        # CG operator product alone; the difference is the vector work and
+        # launch gaps of one CG step
+        A = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=g)
+        K = (A + A.T) * 0.5
+        del A
+        K.diagonal().add_(2.0 * math.sqrt(2.0 * n))  # spectrum in ~[0.6, 3.4] sqrt(2n)
+        p = lrep.Problem.dense(K, K, borrow=True)
+        p.set_options(precision=lrep.PREC_MIXED_BF16X3)
+        B = torch.randn(c, n, dtype=torch.float64, device="cuda", generator=g)
+        X = torch.empty(c, n, dtype=torch.float64, device="cuda")
+        steps = 50
+        prod = []
+        for _ in range(args.reps):
+            ev[0].record()
+            its = p.cg(lrep.OP_K, B, X, 0.0, steps)
+            ev[1].record()
+            torch.cuda.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]) / steps)
+            assert its == steps, its
+            ev[0].record()
+            p.apply(lrep.OP_K, B, X, cg=True)
+            ev[1].record()
+            torch.cuda.synchronize()
+            prod.append(ev[0].elapsed_time(ev[1]))
+        work = {"flops": 6.0 * n * n * c, "bytes": 4.0 * n * n + 16.0 * n * c,
+                "cg_steps_per_call": steps, "ms_per_cg_step": times,
+                "product_ms": prod, "vector_ms_per_step": min(times) - min(prod)}
         p.close()
     elif args.op in ("stencil", "stencil32"):
         # --n is the grid edge; stencil32: the float32 CG product.  X and Y

@@ -509,7 +509,8 @@ struct Solver {
     }));
     // dense operator under the mixed precision: the product's split-K sum
     // runs inside cg_sum_alpha and the directions' bf16 split inside
-    // cg_pdir_split (same arithmetic, two launches and passes fewer)
+    // cg_pdir_split (two launches and passes fewer; the partial sum and
+    // the split taken in fp32)
     const bool fused = cgop && c > 0 && cg_fused(p);
     for (int it = 0; it < maxit; ++it) {
       if (fused) {

@@ -89,6 +89,43 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   return last;
 }
 
+// float64 <-> float32 conversions on the integer units.  GB300 executes
+// every float64 instruction, conversions included, on its FP64 units (about
+// 2 per clock per SM), so a float32 kernel that loads and stores float64
+// data is bound by its conversions.  These rebuild the other format's bit
+// pattern with integer instructions and selects (no branch, no call).
+// f64_to_f32: round to nearest even; results below the float32 normal
+// range flush to a signed zero, overflow gives a signed infinity, NaN stays
+// NaN.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // top 23 mantissa bits
+  const unsigned rest = lo & 0x1FFFFFFFu;                  // the 29 dropped bits
+  unsigned f = sign | ((e - 896u) << 23) | m;
+  // a carry out of the mantissa steps the exponent (to infinity past the
+  // largest float), as rounding to nearest does
+  f += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  const bool nan = e == 0x7FFu && ((hi & 0xFFFFFu) | lo) != 0u;
+  f = e < 897u ? sign : f;
+  f = e > 1150u ? (sign | 0x7F800000u | (nan ? 0x400000u : 0u)) : f;
+  return __uint_as_float(f);
+}
+
+// f32_to_f64: exact for normal numbers, zero, infinities (NaN stays NaN);
+// float32 subnormals flush to a signed zero.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, fe = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  unsigned hi = sign | ((fe + 896u) << 20) | (m >> 3);
+  unsigned lo = u << 29;
+  hi = fe == 0u ? sign : hi;
+  lo = fe == 0u ? 0u : lo;
+  hi = fe == 0xFFu ? (sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u)) : hi;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // Read through L2 (partials written by other blocks of the same launch).
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 

@@ -104,23 +104,23 @@ stencil_z_f32_kernel(int nx, int ny, int nz, float coef, const double* __restric
     const int col = min(c0 + q, c - 1);
     x[q] = X + (int64_t)col * ldx + p0;
     y[q] = Y + (int64_t)col * ldy + p0;
-    below[q] = z0 > 0 ? (float)__ldg(x[q] - plane) : 0.f;
-    cur[q] = (float)__ldg(x[q]);
+    below[q] = z0 > 0 ? f64_to_f32(__ldg(x[q] - plane)) : 0.f;
+    cur[q] = f64_to_f32(__ldg(x[q]));
   }
   const double* dz = d + p0;
   const int ncol = min(SZC, c - c0);
 #pragma unroll 2
   for (int z = z0; z < z1; ++z) {
     const bool up = z + 1 < nz;
-    const float dp = (float)__ldg(dz);
+    const float dp = f64_to_f32(__ldg(dz));
 #pragma unroll
     for (int q = 0; q < SZC; ++q) {
       const double* xq = x[q];
-      const float above = up ? (float)__ldg(xq + plane) : 0.f;
-      const float s4 = (xl ? (float)__ldg(xq - 1) : 0.f) + (xr ? (float)__ldg(xq + 1) : 0.f) +
-                       (yl ? (float)__ldg(xq - nx) : 0.f) + (yr ? (float)__ldg(xq + nx) : 0.f);
+      const float above = up ? f64_to_f32(__ldg(xq + plane)) : 0.f;
+      const float s4 = (xl ? f64_to_f32(__ldg(xq - 1)) : 0.f) + (xr ? f64_to_f32(__ldg(xq + 1)) : 0.f) +
+                       (yl ? f64_to_f32(__ldg(xq - nx)) : 0.f) + (yr ? f64_to_f32(__ldg(xq + nx)) : 0.f);
       const float lap = s4 + below[q] + above - 6.f * cur[q];
-      if (q < ncol) *y[q] = (double)fmaf(coef, lap, dp * cur[q]);
+      if (q < ncol) *y[q] = f32_to_f64(fmaf(coef, lap, dp * cur[q]));
       below[q] = cur[q];
       cur[q] = above;
       x[q] = xq + plane;
@@ -275,7 +275,12 @@ __global__ void cg_pdir_kernel(int64_t n, const double* __restrict__ R,
 }
 
 // cg_alpha_kernel with Q formed first from the split-K partials of the
-// tensor-core product (inactive columns: Q is not needed and not formed)
+// tensor-core product (inactive columns: Q is not needed and not formed).
+// The fp32 partials are summed in fp32, in split order, and converted once:
+// on GB300 every float64 operation (conversions included) runs at ~2 per
+// clock per SM, and the seven float64 additions per entry made this kernel
+// ALU-bound; the fp32 sum adds ~2^-22 relative error to a product that
+// carries ~2^-16.
 __global__ void __launch_bounds__(256)
 cg_sum_alpha_kernel(int64_t n, int nb, const float* __restrict__ part, int splits,
                     const double* __restrict__ P, double* __restrict__ Q, int64_t ld,
@@ -287,8 +292,9 @@ cg_sum_alpha_kernel(int64_t n, int nb, const float* __restrict__ part, int split
   double acc = 0.0;
   if (s.active[col])
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      double q = 0.0;
-      for (int z = 0; z < splits; ++z) q += (double)part[((int64_t)z * nb + col) * n + i];
+      float qf = 0.0f;
+      for (int z = 0; z < splits; ++z) qf += part[((int64_t)z * nb + col) * n + i];
+      const double q = f32_to_f64(qf);
       Q[i + (int64_t)col * ld] = q;
       acc = fma(P[i + (int64_t)col * ld], q, acc);
     }
@@ -308,7 +314,11 @@ cg_sum_alpha_kernel(int64_t n, int nb, const float* __restrict__ part, int split
   }
 }
 
-// cg_pdir_kernel that also writes bf16 hi = bf16(p), lo = bf16(p - hi)
+// cg_pdir_kernel that also writes the bf16 split of the new direction p:
+// with f = fp32(p) (one float64 conversion), hi = bf16(f), lo = bf16(f - hi)
+// (f - hi is exact in fp32).  hi + lo is within ~2^-17 of p, as for a
+// split taken from the float64 value directly, at one float64 operation
+// per entry instead of four.
 __global__ void cg_pdir_split_kernel(int64_t n, const double* __restrict__ R,
                                      double* __restrict__ P, int64_t ld, CgState s,
                                      __nv_bfloat16* __restrict__ hi,
@@ -322,9 +332,10 @@ __global__ void cg_pdir_split_kernel(int64_t n, const double* __restrict__ R,
     const int64_t o = i + (int64_t)col * ld;
     const double pv = fma(b, P[o], R[o]);
     P[o] = pv;
-    const __nv_bfloat16 h = __double2bfloat16(pv);
+    const float f = f64_to_f32(pv);
+    const __nv_bfloat16 h = __float2bfloat16_rn(f);
     hi[i + (int64_t)col * ldb] = h;
-    lo[i + (int64_t)col * ldb] = __double2bfloat16(pv - (double)__bfloat162float(h));
+    lo[i + (int64_t)col * ldb] = __float2bfloat16_rn(f - __bfloat162float(h));
   }
 }
 

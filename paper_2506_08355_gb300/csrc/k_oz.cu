@@ -51,6 +51,18 @@ namespace {
 
 using namespace tc5;
 
+// TMA load of one digit tile: entries [x, x + 64) of rows [y, y + 128) of
+// digit plane z (3-D tensor map; rows or entries past the planes' extent
+// arrive as zeros and are not read from memory)
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(mbar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
 constexpr int S = kOzSlices;  // digits per value
 constexpr int EXACT = 4;      // levels 2..5 drained exactly per k-tile
 constexpr int BM = 128, BK = 64;
@@ -139,7 +151,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ C
           }
           const uint32_t fa = smem_u32(&fullA[st]);
           mbar_expect_tx(fa, TILE_A);
-          tma_load_2d(smem_u32(bufA + st * TILE_A), &mA, fa, k, s * rows_pad + tile_m * BM);
+          tma_load_3d(smem_u32(bufA + st * TILE_A), &mA, fa, k, tile_m * BM, s);
           ia = q + 1;
         }
       }
@@ -478,6 +490,39 @@ bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t outer, 
   return tc_make_map(map, base, inner, outer, ld, BK, box_outer);
 }
 
+// signature of cuTensorMapEncodeTiled (driver API, obtained at run time)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Descriptor of left-operand digit planes: plane s, row r, entry kk at
+// base[(s * rows + r) * ldk + kk] (ldk a multiple of 8), read in boxes of
+// 64 entries x 128 rows x 1 plane with the 128-byte swizzle.  Rows past
+// `rows` (a Gram with fewer than 128 columns) and entries past ldk (a short
+// contraction) are filled with zeros by the copy, so the planes are stored
+// without padding to the tile.
+bool make_planes_map(CUtensorMap* map, const void* base, int64_t ldk, int64_t rows) {
+  static const EncodeTiledFn fn = [] {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn)f;
+    return (EncodeTiledFn) nullptr;
+  }();
+  if (!fn || ldk % 8 != 0 || rows <= 0) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)ldk, (cuuint64_t)rows, (cuuint64_t)S};
+  const cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)(rows * ldk * 2)};
+  const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)BM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 Segs segs_sub(const Segs& s, int j0, int cnt) {
   Segs o{};
   o.nseg = 0;
@@ -524,8 +569,8 @@ cudaError_t slice_columns(const Segs& X, int64_t k, int c, int C, int64_t ldk, u
 }
 
 // one column group: Y[:, 0:c] = alpha Y + beta A X for the sliced left
-// operand A (rows_pad x ldk planes behind mapA, row exponents sig) and the
-// c <= C columns of X
+// operand A (digit planes behind the 3-D map mapA, row exponents sig for
+// rows_pad rows) and the c <= C columns of X
 template <int C>
 cudaError_t oz_group(const CUtensorMap& mapA, int64_t rows, int64_t rows_pad, int64_t ldk,
                      const int* sig, const Segs& X, int64_t k, int c, double* Y, int64_t ldy,
@@ -623,8 +668,7 @@ cudaError_t oz_slice_operator(int64_t n, const double* A, int64_t lda, OzOperand
   cudaError_t e = slice_columns(seg1(A, lda, (int)n), n, (int)n, (int)o->rows_pad, o->ldk,
                                 (uint16_t*)o->slices, o->sig, maxbits, st);
   if (e != cudaSuccess) return e;
-  if (!make_map(&o->map, o->slices, o->ldk, (int64_t)S * o->rows_pad, o->ldk, BM))
-    return cudaErrorInvalidValue;
+  if (!make_planes_map(&o->map, o->slices, o->ldk, o->rows_pad)) return cudaErrorInvalidValue;
   return cudaSuccess;
 }
 
@@ -659,11 +703,14 @@ cudaError_t oz_gram(int64_t n, const Segs& A, const Segs& B, double* G, int64_t 
   int* sig = (int*)w;
   unsigned long long* maxbits = (unsigned long long*)(w + align256((size_t)rp * 4));
   w += align256((size_t)rp * 12) + 512;
-  // rows of A^T = columns of A
-  cudaError_t e = slice_columns(A, n, a, (int)rp, ldk, planes, sig, maxbits, st);
+  // rows of A^T = columns of A: planes of exactly a rows (the copy fills
+  // the tile's rows a..127 with zeros); the exponents of those rows are 0
+  cudaError_t e = slice_columns(A, n, a, a, ldk, planes, sig, maxbits, st);
+  if (e == cudaSuccess && rp > a)
+    e = cudaMemsetAsync(sig + a, 0, (size_t)(rp - a) * sizeof(int), st);
   if (e != cudaSuccess) return e;
   CUtensorMap map;
-  if (!make_map(&map, planes, ldk, (int64_t)S * rp, ldk, BM)) return cudaErrorInvalidValue;
+  if (!make_planes_map(&map, planes, ldk, a)) return cudaErrorInvalidValue;
   return oz_groups(map, a, rp, ldk, sig, B, n, b, G, ldg, 0.0, 1.0, w, err, nullptr, st);
 }
 
@@ -690,13 +737,16 @@ cudaError_t oz_update(int64_t n, int k, int c, double alpha, const Segs& A, cons
       oz_rowslice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (attr != cudaSuccess) return attr;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  oz_rowslice_kernel<<<(unsigned)(rp / kRows), 256, smem, st>>>(A, n, k, ldk, planes,
-                                                                rp * ldk, sig);
+  // left planes with the contraction padded to 8 entries, not to the
+  // 64-entry tile: the copy fills entries k8..63 of the last k-tile with zeros
+  const int64_t k8 = ((int64_t)k + 7) / 8 * 8;
+  oz_rowslice_kernel<<<(unsigned)(rp / kRows), 256, smem, st>>>(A, n, k, k8, planes, rp * k8,
+                                                                sig);
   LREP_COUNT_LAUNCH();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap map;
-  if (!make_map(&map, planes, ldk, (int64_t)S * rp, ldk, BM)) return cudaErrorInvalidValue;
+  if (!make_planes_map(&map, planes, k8, rp)) return cudaErrorInvalidValue;
   return oz_groups(map, n, rp, ldk, sig, seg1(B, ldb, c), k, c, C, ldc, alpha, beta, w, err,
                    nullptr, st);
 }

@@ -132,10 +132,10 @@ cudaError_t cg_pdir(int64_t n, int nb, const double* R, double* P, int64_t ld,
                     CgState& s, cudaStream_t st);
 // Fused steps of the CG on the bf16 hi/lo tensor-core operator:
 // cg_sum_alpha forms Q from the product's split-K partials (fp32,
-// part[(z * nb + j) * n + i], summed over z in order in fp64, as the
-// unfused product does) and then computes alpha as cg_alpha;
-// cg_pdir_split is cg_pdir that also writes the new directions' bf16
-// hi/lo split (the next product's operand, leading dimension ldb).
+// part[(z * nb + j) * n + i], summed over z in order in fp32) and then
+// computes alpha as cg_alpha; cg_pdir_split is cg_pdir that also writes
+// the new directions' bf16 hi/lo split (taken from their fp32 rounding;
+// the next product's operand, leading dimension ldb).
 cudaError_t cg_sum_alpha(int64_t n, int nb, const float* part, int splits, const double* P,
                          double* Q, int64_t ld, CgState& s, cudaStream_t st);
 cudaError_t cg_pdir_split(int64_t n, int nb, const double* R, double* P, int64_t ld,
