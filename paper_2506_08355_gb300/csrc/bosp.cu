@@ -165,7 +165,7 @@ struct Solver {
   size_t ozws_bytes = 0;
   double* part;
   double *Rg, *Rinv, *Rwork;  // r x r scratch of the V0 normalisation
-  unsigned int* counters;  // [0] residual [1] colnorm [2..4] cg
+  unsigned int* counters;  // [0] residual [1] colnorm [2..] cg (128)
   CgState cg;
   // pinned host mirror
   struct Host {
@@ -300,7 +300,7 @@ struct Solver {
     ws = A.take<double>(std::max<size_t>(ws_elems, 1));
     part = A.take<double>(std::max<size_t>(part_elems, 1));
     ozws = oz ? A.take<uint8_t>(ozws_bytes) : nullptr;
-    counters = A.take<unsigned int>(64);
+    counters = A.take<unsigned int>(256);
     cg.rho = A.take<double>(cgcols); cg.stop = A.take<double>(cgcols);
     cg.alpha = A.take<double>(cgcols); cg.beta = A.take<double>(cgcols);
     cg.active = A.take<int>(cgcols); cg.done = A.take<int>(8);
@@ -511,7 +511,10 @@ struct Solver {
     // runs inside cg_sum_alpha and the directions' bf16 split inside
     // cg_pdir_split (two launches and passes fewer; the partial sum and
     // the split taken in fp32)
+    // (in one cooperative launch when the block fits it)
     const bool fused = cgop && c > 0 && cg_fused(p);
+    const bool coop = fused && cg_step_coop_fits(n, c, cg);
+    if (coop) LCK(cudaMemsetAsync(cg.counter + 8, 0, (size_t)c * sizeof(unsigned int), st));
     for (int it = 0; it < maxit; ++it) {
       if (fused) {
         CgFused fb{};
@@ -519,6 +522,11 @@ struct Solver {
           return apply_cg_partials(p, which, c, Pr, ld, it > 0, cg.done, ws, ws_elems, &fb);
         }));
         LST(timed(LREP_PC_CGVEC, [&] {
+          if (coop) {
+            LCK(cg_step_coop(n, c, fb.part, fb.splits, X, Rr, Pr, ld, cg, fb.xhi, fb.xlo, fb.ldb,
+                             it, p->op.tc_err, st));
+            return LREP_OK;
+          }
           LCK(cg_sum_alpha(n, c, fb.part, fb.splits, Pr, Qr, ld, cg, st));
           LCK(cg_update(n, c, X, Rr, Pr, Qr, ld, cg, st));
           LCK(cg_pdir_split(n, c, Rr, Pr, ld, cg, fb.xhi, fb.xlo, fb.ldb, st));

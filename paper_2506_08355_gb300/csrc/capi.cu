@@ -644,21 +644,27 @@ lrep_status lrep_op_cg(lrep_problem p, int32_t op, int32_t ncols, const double* 
   cg.active = A.take<int>(ncols);
   cg.done = A.take<int>(8);
   cg.iters = A.take<int>(8);
-  cg.counter = A.take<unsigned int>(8);
+  cg.counter = A.take<unsigned int>(128);
   cg.part = A.take<double>(cg_part_elems(n, ncols));
   double* ws = A.take<double>(aws + 1);
   if (!ws) return p->fail(LREP_ERR_NOMEM, "lrep_op_cg: workspace layout overflow");
   PCK(p, cudaMemsetAsync(cg.done, 0, 8 * sizeof(int), p->stream));
   PCK(p, cudaMemsetAsync(cg.iters, 0, 8 * sizeof(int), p->stream));
-  PCK(p, cudaMemsetAsync(cg.counter, 0, 8 * sizeof(unsigned int), p->stream));
+  PCK(p, cudaMemsetAsync(cg.counter, 0, 128 * sizeof(unsigned int), p->stream));
   PCK(p, cg_init(n, ncols, B, ldb, X, R, P, ldx, tol, cg, p->stream));
   const bool fused = cg_fused(p);  // as in the solver's CG
+  const bool coop = fused && cg_step_coop_fits(n, ncols, cg);
   for (int it = 0; it < maxit; ++it) {
     if (fused) {
       CgFused fb{};
       const lrep_status s =
           apply_cg_partials(p, op, ncols, P, ldx, it > 0, cg.done, ws, aws, &fb);
       if (s != LREP_OK) return s;
+      if (coop) {
+        PCK(p, cg_step_coop(n, ncols, fb.part, fb.splits, X, R, P, ldx, cg, fb.xhi, fb.xlo,
+                            fb.ldb, it, p->op.tc_err, p->stream));
+        continue;
+      }
       PCK(p, cg_sum_alpha(n, ncols, fb.part, fb.splits, P, Q, ldx, cg, p->stream));
       PCK(p, cg_update(n, ncols, X, R, P, Q, ldx, cg, p->stream));
       PCK(p, cg_pdir_split(n, ncols, R, P, ldx, cg, fb.xhi, fb.xlo, fb.ldb, p->stream));

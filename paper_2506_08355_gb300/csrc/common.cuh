@@ -113,6 +113,21 @@ __device__ __forceinline__ float f64_to_f32(double x) {
   return __uint_as_float(f);
 }
 
+// f64_to_f32_rz: rounded toward zero (error below 2^-23 relative, the float
+// kernels' own rounding), half the instructions of f64_to_f32: the float
+// pattern is the double's top bits with the exponent rebased, computed
+// modulo 2^9 in the exponent field (exact for biased exponents 897..1150);
+// smaller magnitudes flush to a signed zero, larger ones and NaN give a
+// signed infinity.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned mag = hi & 0x7FFFFFFFu;
+  unsigned f = ((mag << 3) | (lo >> 29)) - (896u << 23);
+  f = mag < (897u << 20) ? 0u : f;
+  f = mag >= (1151u << 20) ? 0x7F800000u : f;
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
 // f32_to_f64: exact for normal numbers, zero, infinities (NaN stays NaN);
 // float32 subnormals flush to a signed zero.
 __device__ __forceinline__ double f32_to_f64(float f) {

@@ -76,9 +76,12 @@ stencil_kernel(int nx, int ny, int nz, double coef_d, const double* __restrict__
 // 2.5-D form, four columns per thread, but no shared memory and no
 // barriers: the x and y neighbours are the tile's own loads of the same
 // plane (L1 hits), the z neighbours stay in registers, and the warps march
-// independently with the next planes' loads in flight.  The float64
-// products stay on the 2.5-D form, which is bound by the FP64 pipe on
-// GB300 (~8 FP64 operations per point and column) either way.
+// independently with the next planes' loads in flight.  Loads are narrowed
+// to float32 by truncation on the integer units and the result widened
+// exactly (a hardware conversion is a float64 instruction on GB300, ~2 per
+// clock per SM).  The float64 products stay on the 2.5-D form, which is
+// bound by the FP64 pipe on GB300 (~8 FP64 operations per point and column)
+// either way.
 constexpr int SZC = 4;  // columns per thread
 
 __global__ void __launch_bounds__(STX * STY)
@@ -104,21 +107,23 @@ stencil_z_f32_kernel(int nx, int ny, int nz, float coef, const double* __restric
     const int col = min(c0 + q, c - 1);
     x[q] = X + (int64_t)col * ldx + p0;
     y[q] = Y + (int64_t)col * ldy + p0;
-    below[q] = z0 > 0 ? f64_to_f32(__ldg(x[q] - plane)) : 0.f;
-    cur[q] = f64_to_f32(__ldg(x[q]));
+    below[q] = z0 > 0 ? f64_to_f32_rz(__ldg(x[q] - plane)) : 0.f;
+    cur[q] = f64_to_f32_rz(__ldg(x[q]));
   }
   const double* dz = d + p0;
   const int ncol = min(SZC, c - c0);
 #pragma unroll 2
   for (int z = z0; z < z1; ++z) {
     const bool up = z + 1 < nz;
-    const float dp = f64_to_f32(__ldg(dz));
+    const float dp = f64_to_f32_rz(__ldg(dz));
 #pragma unroll
     for (int q = 0; q < SZC; ++q) {
       const double* xq = x[q];
-      const float above = up ? f64_to_f32(__ldg(xq + plane)) : 0.f;
-      const float s4 = (xl ? f64_to_f32(__ldg(xq - 1)) : 0.f) + (xr ? f64_to_f32(__ldg(xq + 1)) : 0.f) +
-                       (yl ? f64_to_f32(__ldg(xq - nx)) : 0.f) + (yr ? f64_to_f32(__ldg(xq + nx)) : 0.f);
+      const float above = up ? f64_to_f32_rz(__ldg(xq + plane)) : 0.f;
+      const float s4 = (xl ? f64_to_f32_rz(__ldg(xq - 1)) : 0.f) +
+                       (xr ? f64_to_f32_rz(__ldg(xq + 1)) : 0.f) +
+                       (yl ? f64_to_f32_rz(__ldg(xq - nx)) : 0.f) +
+                       (yr ? f64_to_f32_rz(__ldg(xq + nx)) : 0.f);
       const float lap = s4 + below[q] + above - 6.f * cur[q];
       if (q < ncol) *y[q] = f32_to_f64(fmaf(coef, lap, dp * cur[q]));
       below[q] = cur[q];
@@ -339,6 +344,193 @@ __global__ void cg_pdir_split_kernel(int64_t n, const double* __restrict__ R,
   }
 }
 
+// ------------------------------------------------- one-launch CG step
+// cg_sum_alpha + cg_update + cg_pdir_split in one cooperative launch: the
+// CTA of (slab, column) keeps its rows of p and q (later r) in registers
+// across the three phases, and the two reductions of the step (p.q for
+// alpha, r.r for beta) are barriers over the column's CTAs instead of
+// kernel boundaries.  Every CTA reads its column's state (active, rho,
+// stop) at entry and derives alpha and beta from the column's partials in
+// a fixed order; CTA (0, 0) alone writes the new state of every column,
+// after every column has passed its second barrier, so no state is read
+// after it is rewritten.  Same arithmetic as the three kernels, with the
+// per-thread row order of this kernel's slabs.
+constexpr int kCoopRows = 8;                        // rows per thread
+constexpr int kCoopMaxCols = 120;                   // column barriers in CgState.counter
+constexpr long long kBarrierCycles = 4000000000ll;  // ~2 s of SM clock
+
+// Wait until *count >= target (thread 0 of the CTA); bounded: on expiry
+// *err is set to 6 and false returned.
+__device__ __forceinline__ bool wait_count(const unsigned int* count, unsigned int target,
+                                           int* err) {
+  const long long t0 = clock64();
+  while (*(const volatile unsigned int*)count < target) {
+    if (clock64() - t0 > kBarrierCycles) {
+      if (err) atomicExch(err, 6);
+      return false;
+    }
+    __nanosleep(100);
+  }
+  return true;
+}
+
+// Barrier over the CTAs that share `count` (one arrival per CTA per
+// barrier; the k-th barrier of the CG solve waits for k * members).
+__device__ __forceinline__ bool group_barrier(unsigned int* count, unsigned int target,
+                                              int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    ok = wait_count(count, target, err) ? 1 : 0;
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(256, 4)
+cg_step_coop_kernel(int64_t n, int nb, const float* __restrict__ part, int splits,
+                    double* __restrict__ X, double* __restrict__ R, double* __restrict__ P,
+                    int64_t ld, CgState s, __nv_bfloat16* __restrict__ hi,
+                    __nv_bfloat16* __restrict__ lo, int64_t ldb, int64_t slab_rows, int epoch,
+                    int* err) {
+  if (*s.done) return;
+  __shared__ double red[32];
+  __shared__ double sh_sum;
+  const int col = blockIdx.y, slab = blockIdx.x, slabs = gridDim.x;
+  unsigned int* bar = s.counter + 8;  // one barrier counter per column
+  const unsigned int t1 = (unsigned int)(2 * epoch + 1) * slabs, t2 = t1 + slabs;
+  const int64_t r0 = (int64_t)slab * slab_rows, r1 = min(n, r0 + slab_rows);
+  const int64_t cx = (int64_t)col * ld;
+  const bool act0 = s.active[col] != 0;
+  const double rho = s.rho[col], stop = s.stop[col];
+  double* part1 = s.part;                        // p.q partials
+  double* part2 = s.part + (int64_t)nb * slabs;  // r.r partials
+  double pr[kCoopRows], qr[kCoopRows];
+  // phase 1: q = A p from the split-K partials (split order, every row's
+  // partial of one split in flight together), p.q
+  float qf[kCoopRows];
+#pragma unroll
+  for (int k = 0; k < kCoopRows; ++k) qf[k] = 0.0f;
+  if (act0)
+    for (int z = 0; z < splits; ++z) {
+      const float* pz = part + ((int64_t)z * nb + col) * n;
+#pragma unroll
+      for (int k = 0; k < kCoopRows; ++k) {
+        const int64_t i = r0 + threadIdx.x + (int64_t)k * blockDim.x;
+        if (i < r1) qf[k] += pz[i];
+      }
+    }
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < kCoopRows; ++k) {
+    const int64_t i = r0 + threadIdx.x + (int64_t)k * blockDim.x;
+    pr[k] = 0.0;
+    qr[k] = 0.0;
+    if (act0 && i < r1) {
+      qr[k] = f32_to_f64(qf[k]);
+      pr[k] = P[i + cx];
+      acc = fma(pr[k], qr[k], acc);
+    }
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part1[(int64_t)col * slabs + slab] = acc;
+  if (!group_barrier(bar + col, t1, err)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int z = 0; z < slabs; ++z) t += ld_cg(part1 + (int64_t)col * slabs + z);
+    sh_sum = t;
+  }
+  __syncthreads();
+  const double pq = sh_sum;
+  const bool act1 = act0 && pq > 0.0 && isfinite(pq);
+  const double alpha = act1 ? rho / pq : 0.0;
+  // phase 2: x += alpha p, r -= alpha q, r.r
+  double acc2 = 0.0;
+  if (act1) {
+#pragma unroll
+    for (int k = 0; k < kCoopRows; ++k) {
+      const int64_t i = r0 + threadIdx.x + (int64_t)k * blockDim.x;
+      if (i < r1) {
+        const int64_t o = i + cx;
+        X[o] = fma(alpha, pr[k], X[o]);
+        const double r = fma(-alpha, qr[k], R[o]);
+        R[o] = r;
+        qr[k] = r;
+        acc2 = fma(r, r, acc2);
+      }
+    }
+  }
+  acc2 = block_sum(acc2, red);
+  if (threadIdx.x == 0) part2[(int64_t)col * slabs + slab] = acc2;
+  if (!group_barrier(bar + col, t2, err)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int z = 0; z < slabs; ++z) t += ld_cg(part2 + (int64_t)col * slabs + z);
+    sh_sum = t;
+  }
+  __syncthreads();
+  const double rn = sh_sum;
+  const bool act2 = act1 && rn > stop && isfinite(rn);
+  // phase 3: p = r + beta p and its bf16 split
+  if (act2) {
+    const double beta = rn / rho;
+#pragma unroll
+    for (int k = 0; k < kCoopRows; ++k) {
+      const int64_t i = r0 + threadIdx.x + (int64_t)k * blockDim.x;
+      if (i < r1) {
+        const double pv = fma(beta, pr[k], qr[k]);
+        P[i + cx] = pv;
+        const float f = f64_to_f32(pv);
+        const __nv_bfloat16 h = __float2bfloat16_rn(f);
+        hi[i + (int64_t)col * ldb] = h;
+        lo[i + (int64_t)col * ldb] = __float2bfloat16_rn(f - __bfloat162float(h));
+      }
+    }
+  }
+  // the new state of every column (CTA (0, 0) only, once every column has
+  // passed its second barrier)
+  if (slab == 0 && col == 0) {
+    __shared__ int any, all_ok;
+    if (threadIdx.x == 0) {
+      any = 0;
+      all_ok = 1;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nb; c += blockDim.x)
+      if (!wait_count(bar + c, t2, err)) atomicExch(&all_ok, 0);
+    __syncthreads();
+    if (!all_ok) return;
+    __threadfence();
+    for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+      if (!s.active[c]) {
+        s.alpha[c] = 0.0;
+        continue;
+      }
+      double q = 0.0, r = 0.0;
+      for (int z = 0; z < slabs; ++z) q += ld_cg(part1 + (int64_t)c * slabs + z);
+      if (!(q > 0.0 && isfinite(q))) {
+        s.alpha[c] = 0.0;
+        s.active[c] = 0;
+        continue;
+      }
+      s.alpha[c] = s.rho[c] / q;
+      for (int z = 0; z < slabs; ++z) r += ld_cg(part2 + (int64_t)c * slabs + z);
+      s.beta[c] = r / s.rho[c];
+      s.rho[c] = r;
+      if (!(r > s.stop[c]) || !isfinite(r)) s.active[c] = 0;
+      if (s.active[c]) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *s.done = any ? 0 : 1;
+      if (s.iters) *s.iters += 1;
+    }
+  }
+}
+
 int cg_slabs(int64_t n) { return reduction_slabs(n, 2048, 64); }
 unsigned grid_rows(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2 * kNumSMs));
@@ -391,7 +583,36 @@ cudaError_t csr_apply_f64(int64_t n, const int64_t* rp, const int32_t* ci,
   return cudaGetLastError();
 }
 
-size_t cg_part_elems(int64_t n, int nb) { return (size_t)cg_slabs(n) * nb; }
+// two partial sets: the one-launch CG step keeps p.q and r.r apart
+size_t cg_part_elems(int64_t n, int nb) { return (size_t)2 * cg_slabs(n) * nb; }
+
+bool cg_step_coop_fits(int64_t n, int nb, const CgState& s) {
+  if (nb < 1 || nb > kCoopMaxCols || s.slabs < 1) return false;
+  const int64_t sr = (n + s.slabs - 1) / s.slabs;
+  if (sr > (int64_t)kCoopRows * 256) return false;
+  int dev = 0, sms = 0, per = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, cg_step_coop_kernel, 256, 0) !=
+          cudaSuccess)
+    return false;
+  return coop != 0 && (int64_t)s.slabs * nb <= (int64_t)per * sms;
+}
+
+cudaError_t cg_step_coop(int64_t n, int nb, const float* part, int splits, double* X,
+                         double* R, double* P, int64_t ld, CgState& s, void* hi, void* lo,
+                         int64_t ldb, int epoch, int* err, cudaStream_t st) {
+  int64_t sr = (n + s.slabs - 1) / s.slabs;
+  __nv_bfloat16* h = (__nv_bfloat16*)hi;
+  __nv_bfloat16* l = (__nv_bfloat16*)lo;
+  void* args[] = {&n,  &nb, &part, &splits, &X,   &R,     &P,  &ld,
+                  &s,  &h,  &l,    &ldb,    &sr, &epoch, &err};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)cg_step_coop_kernel,
+                                                    dim3(s.slabs, nb), dim3(256), args, 0, st);
+  LREP_COUNT_LAUNCH();
+  return e;
+}
 
 cudaError_t cg_init(int64_t n, int nb, const double* B, int64_t ldb, double* X,
                     double* R, double* P, int64_t ld, double tol, CgState& s,

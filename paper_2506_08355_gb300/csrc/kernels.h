@@ -116,7 +116,7 @@ struct CgState {  // device arrays of length nb (+ counters)
   int* active;
   int* done;      // all columns converged
   double* part;   // partials: nb * slabs
-  unsigned int* counter;  // 3 counters, zero-initialised
+  unsigned int* counter;  // 128 counters, zero-initialised
   int* iters;     // iterations with an active column (device counter)
   int slabs;
 };
@@ -140,6 +140,16 @@ cudaError_t cg_sum_alpha(int64_t n, int nb, const float* part, int splits, const
                          double* Q, int64_t ld, CgState& s, cudaStream_t st);
 cudaError_t cg_pdir_split(int64_t n, int nb, const double* R, double* P, int64_t ld,
                           CgState& s, void* hi, void* lo, int64_t ldb, cudaStream_t st);
+// The three fused steps above in one cooperative launch (per-column
+// barriers for the two reductions of a CG step), when n, nb fit it
+// (cg_step_coop_fits: slabs of at most 2048 rows, nb <= 120, every CTA
+// co-resident).  CgState.counter[8 .. 8 + nb) are the column barrier
+// counters: zero at the start of a CG solve, epoch = the solve's step
+// index.  A barrier that does not complete within ~2 s sets *err to 6.
+bool cg_step_coop_fits(int64_t n, int nb, const CgState& s);
+cudaError_t cg_step_coop(int64_t n, int nb, const float* part, int splits, double* X,
+                         double* R, double* P, int64_t ld, CgState& s, void* hi, void* lo,
+                         int64_t ldb, int epoch, int* err, cudaStream_t st);
 
 // ------------------------------------------------------------ small (1 CTA)
 // Small LREP of order d (batched: one CTA per problem).  Per problem:
