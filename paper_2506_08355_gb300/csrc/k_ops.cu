@@ -84,7 +84,7 @@ stencil_kernel(int nx, int ny, int nz, double coef_d, const double* __restrict__
 // either way.
 constexpr int SZC = 4;  // columns per thread
 
-__global__ void __launch_bounds__(STX * STY)
+__global__ void __launch_bounds__(STX * STY, 5)
 stencil_z_f32_kernel(int nx, int ny, int nz, float coef, const double* __restrict__ d,
                      int c, const double* __restrict__ X, int64_t ldx,
                      double* __restrict__ Y, int64_t ldy, int zchunk, int tiles_x,
@@ -398,7 +398,7 @@ cg_step_coop_kernel(int64_t n, int nb, const float* __restrict__ part, int split
                     int* err) {
   if (*s.done) return;
   __shared__ double red[32];
-  __shared__ double sh_sum;
+  __shared__ double sh_coef;
   const int col = blockIdx.y, slab = blockIdx.x, slabs = gridDim.x;
   unsigned int* bar = s.counter + 8;  // one barrier counter per column
   const unsigned int t1 = (unsigned int)(2 * epoch + 1) * slabs, t2 = t1 + slabs;
@@ -438,15 +438,15 @@ cg_step_coop_kernel(int64_t n, int nb, const float* __restrict__ part, int split
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) part1[(int64_t)col * slabs + slab] = acc;
   if (!group_barrier(bar + col, t1, err)) return;
+  // alpha (thread 0: one float64 division per CTA)
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int z = 0; z < slabs; ++z) t += ld_cg(part1 + (int64_t)col * slabs + z);
-    sh_sum = t;
+    double pq = 0.0;
+    for (int z = 0; z < slabs; ++z) pq += ld_cg(part1 + (int64_t)col * slabs + z);
+    sh_coef = (act0 && pq > 0.0 && isfinite(pq)) ? rho / pq : 0.0;
   }
   __syncthreads();
-  const double pq = sh_sum;
-  const bool act1 = act0 && pq > 0.0 && isfinite(pq);
-  const double alpha = act1 ? rho / pq : 0.0;
+  const double alpha = sh_coef;
+  const bool act1 = alpha != 0.0;
   // phase 2: x += alpha p, r -= alpha q, r.r
   double acc2 = 0.0;
   if (act1) {
@@ -466,17 +466,16 @@ cg_step_coop_kernel(int64_t n, int nb, const float* __restrict__ part, int split
   acc2 = block_sum(acc2, red);
   if (threadIdx.x == 0) part2[(int64_t)col * slabs + slab] = acc2;
   if (!group_barrier(bar + col, t2, err)) return;
+  // beta (thread 0), -1 when the column stops
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int z = 0; z < slabs; ++z) t += ld_cg(part2 + (int64_t)col * slabs + z);
-    sh_sum = t;
+    double rn = 0.0;
+    for (int z = 0; z < slabs; ++z) rn += ld_cg(part2 + (int64_t)col * slabs + z);
+    sh_coef = (act1 && rn > stop && isfinite(rn)) ? rn / rho : -1.0;
   }
   __syncthreads();
-  const double rn = sh_sum;
-  const bool act2 = act1 && rn > stop && isfinite(rn);
+  const double beta = sh_coef;
   // phase 3: p = r + beta p and its bf16 split
-  if (act2) {
-    const double beta = rn / rho;
+  if (beta >= 0.0) {
 #pragma unroll
     for (int k = 0; k < kCoopRows; ++k) {
       const int64_t i = r0 + threadIdx.x + (int64_t)k * blockDim.x;
@@ -556,10 +555,31 @@ cudaError_t stencil_apply(bool f32, int nx, int ny, int nz, double coef_h2, cons
   const int zchunk = (nz + zchunks - 1) / zchunks;
   zchunks = (nz + zchunk - 1) / zchunk;
   if (f32) {
+    // z chunks (of >= 4 planes): fewest waves of the resident slots times
+    // (planes per chunk + the 2 planes a chunk loads before its first)
     const int cgrp = (c + SZC - 1) / SZC;
-    int zc = (int)std::max<int64_t>(1, (4 * kNumSMs + (int64_t)tiles * cgrp - 1) /
-                                           ((int64_t)tiles * cgrp));
-    zc = std::min(zc, std::max(1, nz / 4));
+    static const int64_t slots = [] {
+      int per = 0, dev = 0, sms = kNumSMs;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stencil_z_f32_kernel, STX * STY,
+                                                        0) != cudaSuccess ||
+          per < 1)
+        return (int64_t)4 * kNumSMs;
+      return (int64_t)per * sms;
+    }();
+    const int64_t unit = (int64_t)tiles * cgrp;
+    int zc = 1;
+    int64_t best = -1;
+    for (int t = 1; t <= std::max(1, nz / 4); ++t) {
+      const int tch = (nz + t - 1) / t;
+      const int64_t w = unit * ((nz + tch - 1) / tch);
+      const int64_t cost = ((w + slots - 1) / slots) * (tch + 2);
+      if (best < 0 || cost < best) {
+        best = cost;
+        zc = t;
+      }
+    }
     const int zch = (nz + zc - 1) / zc;
     zc = (nz + zch - 1) / zch;
     stencil_z_f32_kernel<<<dim3(tiles, zc, cgrp), STX * STY, 0, st>>>(

@@ -288,8 +288,9 @@ def test_cg_matches_oracle_columnwise(L, prec_name):
 @pytest.mark.parametrize("n,c", [(3000, 12), (8192, 32)])
 def test_cg_mixed_matches_oracle_columnwise(L, prec_name, n, c):
     """The CG of eq. block_GS on the bf16 hi/lo tensor-core operator
-    (lrep_op_cg: the product's split-K sum runs inside cg_sum_alpha, the new
-    directions' bf16 split inside cg_pdir_split) against the oracle's
+    (lrep_op_cg: each step is the tensor-core product plus the one-launch
+    CG step kernel, which sums the product's split-K partials, updates x, r
+    and p and writes the next product's bf16 operand) against the oracle's
     float64 cg, column by column.  The products carry ~2^-16 relative error,
     which moves the iterates by ~1e-5 of the column's norm over 12 steps
     (a numpy model of the split gives 9e-6), so the bound is 1e-4; with the
