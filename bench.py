@@ -762,8 +762,8 @@ KERNELS = {  # the kernels behind each profiled class of solver work
     "gram": "gram_kernel / sliced Gram (oz_colslice + oz_gemm + oz_reduce)",
     "update": "update_kernel / sliced update (oz_rowslice + oz_gemm + oz_reduce)",
     "small": "small_front_kernel + FP64 refinement / small_lrep_one_kernel, small_pq",
-    "cg_vec": ("cg_alpha + cg_update + cg_pdir (dense mixed precision: cg_sum_alpha "
-               "+ cg_update + cg_pdir_split, the product's split-K sum and the "
+    "cg_vec": ("cg_alpha + cg_update + cg_pdir (dense mixed precision: one "
+               "cg_step_coop_kernel per step, the product's split-K sum and the "
                "directions' bf16 split fused in)"),
     "alg1": "biorth_coef_kernel / biorth_lu_kernel",
     "other": "residual, right-hand-side and column-norm kernels",
